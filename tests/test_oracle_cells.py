@@ -80,3 +80,23 @@ def test_wrap_into_box():
     assert np.allclose(k, np.round(k), atol=1e-12)
     assert np.all(y[0] == 0.0)
     assert np.all(y[3] == 0.0)
+
+
+def test_wrap_just_below_multiples_of_the_box():
+    # x one ulp below k*L: x/L can round up to k, so x - L*floor(x/L) is a tiny
+    # negative number that must still land inside [0, L)
+    for Lx in (7.3, 10.0, 12.7, 3.3, 23.99):
+        xs = []
+        for k in range(-6, 7):
+            for t in range(1, 4):
+                x = k * Lx
+                for _ in range(t):
+                    x = np.nextafter(x, -np.inf)
+                xs.append(x)
+                xs.append(np.nextafter(k * Lx, np.inf))
+        x = np.array(xs)
+        pos = np.stack([x, np.full_like(x, 0.5), np.full_like(x, 0.5)], axis=1)
+        s = _sys((Lx, 5.0, 5.0), x.size)
+        y = O.wrap(s, pos)[:, 0]
+        assert np.all(y >= 0.0) and np.all(y < Lx)
+
