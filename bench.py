@@ -1,0 +1,335 @@
+#!/usr/bin/env python
+"""Benchmark of the DPD step loop (arxiv 1804.06205, Fig. 1) on GB300.
+
+One step = position update + wrap + cell division + pair forces (eqs. 3-4
+with Groot-Warren dissipative/random terms) + bonds + velocity update, for
+the whole system, on the device.
+
+Default workload: the 100^3 periodic box at rho = 3 (N = 3,000,000), types
+A/B 50/50, a_AA = a_BB = 25, a_AB = 30, gamma = 4.5, kT = 1, dt = 0.04;
+synthetic, seeded.  Prints ONE JSON line (rank 0):
+  value   FP32 particle-steps/s, state resident in HBM (CUDA-graph replay)
+  e2e     the same metric through the public API with host buffers: every
+          step sets the state from pinned host memory, steps, reads it back
+  fp64_plain  the plain FP64 path, one system per launch
+  roofline    the pair kernel (dominant) against the ALU issue peak
+  cpu_baseline  the FP64 oracle (cell-list mode) on the host cores
+
+--impl reference times the FP64 CPU oracle (the only reference: the paper
+publishes no code) on a bounded sample of the same workload.
+Multi-GPU: replicas only (each rank advances its own copy; value sums them).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s at N=3M rho=3 (FP32 vs FP64 plain); batched p50/p99 latency"
+UNIT = "particle-steps/s"
+WORKLOAD_DESC = ("fluid_3m: periodic 100^3 box, rho=3, N=3,000,000, types A/B 50/50, "
+                 "a_AA=a_BB=25, a_AB=30, gamma=4.5 (sigma=3), kT=1, dt=0.04, lambda=0.65")
+
+# Algorithmic work of one pair-force evaluation (per bead, per step, rho = 3),
+# counted from the method: each unique candidate pair in the 27-cell half
+# shell (40.5 per bead) costs a distance test of 7 ops (3 sub, 3 mul/fma,
+# 1 compare); each unique pair within r_c (6.28 per bead) costs 103 ops
+# (r, w, e, v_ij.e: 13; Philox4x32-10: 60; two uniforms: 6; Box-Muller: 6;
+# scalar force: 8; vector force: 3; add to both beads: 6; id order: 2).
+PAIR_OPS_PER_BEAD = 40.5 * 7 + 6.28 * 103
+# Minimum HBM bytes of the other phases (per bead per step, FP32 path):
+# update+sort reads pos/key/vel/frc (52 B) and writes pos/key/rank (24 B),
+# then the gather moves pos/key/vel/frc/id (56 B) and writes v~ (16 B) plus
+# the index arrays (~24 B): 172 B; bonds+velocity read f_pair/vel/frc/id
+# (52 B) and write vel/frc (32 B): 84 B.
+SORT_BYTES_PER_BEAD = 172.0
+BOND_BYTES_PER_BEAD = 84.0
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    out = {"hbm_gbs": 6800.0, "source": "fallback", "sm_max_mhz": 2070.0}
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained"):
+                if k in d:
+                    out[k] = float(d[k])
+            out["source"] = "measured"
+            for k in ("sm_max_mhz", "clocks_sm_max_mhz"):
+                if k in d:
+                    out["sm_max_mhz"] = float(d[k])
+        except Exception:
+            pass
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", "dpd_clocks_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_cpu_oracle(w, warmup, steps):
+    """The FP64 oracle's cell-list mode on all host cores."""
+    import oracle as O
+    s = O.System(w.L, w.types, w.a, w.gamma, w.kT, w.dt, w.lam, seed=w.seed, bonds=w.bonds)
+    st = O.State(s, w.pos, w.vel, 0, mode=O.MODE_CELLS)
+    st.run(warmup)
+    t0 = time.perf_counter()
+    st.run(steps)
+    dt = time.perf_counter() - t0
+    return w.n * steps / dt, dt, O.num_threads()
+
+
+def reference_arm(args):
+    from paper_1804_06205_gb300 import workloads as W
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    # bounded sample: same density, composition and parameters, 40^3 box
+    L = args.ref_box
+    w = W.fluid(L, ntypes=2, a_same=25.0, a_cross=30.0, seed=1004, name="fluid_3m_sample")
+    value, secs, cores = run_cpu_oracle(w, args.warmup, args.steps)
+    sample = ("FP64 oracle, cell-list mode, %d^3 box of the same fluid (N=%d), %d warm-up + "
+              "%d timed steps" % (L, w.n, args.warmup, args.steps))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fluid_3m")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--fp64-steps", type=int, default=None)
+    ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--ref-box", type=int, default=40)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    from paper_1804_06205_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_1804_06205_gb300 import dpd as D
+    from paper_1804_06205_gb300 import workloads as W
+
+    w = W.make(args.workload)
+    # a dedicated stream: the legacy default stream cannot be graph-captured
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    peaks = _peaks()
+
+    def timed(prec, warmup, steps, profile=True, sampler=None):
+        g = D.System.from_workload(w, precision=prec, cuda_stream=stream.cuda_stream)
+        g.set_state(w.pos, w.vel, 0)
+        g.step(warmup)
+        barrier()
+        if sampler:
+            sampler.start()
+        l0 = g.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step(steps)
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        launches = g.launch_count() - l0
+        clocks = sampler.stop() if sampler else None
+        g.sync()
+        phases = None
+        if profile:
+            g.profile_begin(steps)
+            g.step(steps)
+            pms, pn = g.profile_end()
+            phases = (pms / max(pn, 1)).tolist()
+        pairs = int(g.gr_counts(1.0, 1)[0])
+        g.close()
+        return ms, launches, clocks, phases, pairs
+
+    # ---- FP32, state resident in HBM
+    sampler = ClockSampler(local)
+    ms32, launches, clocks, phases, pairs = timed(D.DPD_FP32, args.warmup, args.steps,
+                                                  sampler=sampler)
+    ms32 = max_over_ranks(ms32)
+    value = ws * w.n * args.steps / (ms32 * 1e-3)
+
+    # ---- plain FP64 path
+    fp64 = None
+    if not args.no_fp64:
+        k64 = args.fp64_steps or args.steps
+        ms64, _, _, ph64, _ = timed(D.DPD_FP64, max(3, args.warmup // 4), k64)
+        ms64 = max_over_ranks(ms64)
+        v64 = ws * w.n * k64 / (ms64 * 1e-3)
+        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / k64, "steps": k64,
+                "phases_ms": dict(zip(("update_sort", "pair", "bond_vel"), ph64)),
+                "fp32_speedup": value / v64}
+
+    # ---- end to end through the public API with pinned host buffers
+    g = D.System.from_workload(w, precision=D.DPD_FP32, cuda_stream=stream.cuda_stream)
+    pos_h = torch.from_numpy(np.ascontiguousarray(w.pos)).pin_memory()
+    vel_h = torch.from_numpy(np.ascontiguousarray(w.vel)).pin_memory()
+    g.set_state_ptr(pos_h.data_ptr(), vel_h.data_ptr(), 0)
+    for _ in range(2):
+        g.step(1)
+        g.get_state_ptr(pos_h.data_ptr(), vel_h.data_ptr())
+    barrier()
+    t0 = time.perf_counter()
+    step = 2
+    for _ in range(args.e2e_steps):
+        g.set_state_ptr(pos_h.data_ptr(), vel_h.data_ptr(), step)
+        g.step(1)
+        step = g.get_state_ptr(pos_h.data_ptr(), vel_h.data_ptr())
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    g.close()
+    e2e = {"value": ws * w.n * args.e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 2 * w.n * 3 * 8, "d2h_bytes_per_step": 2 * w.n * 3 * 8,
+           "steps": args.e2e_steps,
+           "note": "per step: dpd_set_state from pinned host (pos, vel) incl. its force "
+                   "evaluation, dpd_step(1), dpd_get_state to pinned host (pos, vel)"}
+
+    # ---- roofline of the pair kernel (plain-ALU bound)
+    pair_ms = phases[1]
+    alu_peak = 152 * 128 * peaks["sm_max_mhz"] * 1e6          # lane-ops/s at max SM clock
+    achieved = PAIR_OPS_PER_BEAD * w.n / (pair_ms * 1e-3)
+    roofline = {"bound": "alu", "kernel": "k_pair", "achieved": achieved / 1e12,
+                "peak": alu_peak / 1e12, "unit": "Tops/s", "frac": achieved / alu_peak,
+                "traffic": None,
+                "ops_per_bead": PAIR_OPS_PER_BEAD, "launch_ms": pair_ms,
+                "peak_source": "152 SMs x 128 lanes x %.0f MHz (one op per lane per cycle)"
+                               % peaks["sm_max_mhz"]}
+    step_ms = ms32 / args.steps
+    other = {
+        "update_sort": {"ms": phases[0], "bytes_per_bead": SORT_BYTES_PER_BEAD,
+                        "GBs": SORT_BYTES_PER_BEAD * w.n / (phases[0] * 1e-3) / 1e9},
+        "bond_vel": {"ms": phases[2], "bytes_per_bead": BOND_BYTES_PER_BEAD,
+                     "GBs": BOND_BYTES_PER_BEAD * w.n / (phases[2] * 1e-3) / 1e9},
+        "hbm_peak_GBs": peaks["hbm_gbs"], "peak_source": peaks["source"]}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, secs, cores = run_cpu_oracle(w, 1, args.cpu_steps)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "FP64 oracle, cell-list mode, full fluid_3m (N=3,000,000), 1 warm-up + "
+                         "%d timed steps on all host cores" % args.cpu_steps}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD_DESC, "N": w.n,
+                           "l2": "inputs larger than L2 (~0.5 GB of state per replica)",
+                           "parallelism": "replicas" if ws > 1 else "single"},
+                "pair_interactions_per_s": ws * pairs * args.steps / (ms32 * 1e-3),
+                "phases_ms": dict(zip(("update_sort", "pair", "bond_vel"), phases)),
+                "fp64_plain": fp64, "roofline": roofline, "roofline_hbm_phases": other,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,196 @@
+/*
+ * libdpd -- C ABI of the GB300 (sm_103a) engine for the DPD step loop of
+ * arxiv 1804.06205 ("A portable code for dissipative particle dynamics (DPD)
+ * simulations with additional specific interactions", CAMUS).
+ *
+ * The calls follow the paper's statement of the problem:
+ *   - eq. 1-2: Newtonian motion, dr/dt = v, m dv/dt = f, all masses 1;
+ *   - eq. 3:   f_i = sum_{j != i} (F^C + F^D + F^R + F^S), no exclusions;
+ *   - eq. 4:   F^C = a_ij (1 - r) e_ij for r < r_c = 1 (soft repulsion);
+ *   - F^D, F^R (named in the paper, forms of Groot and Warren):
+ *              F^D = -gamma (1 - r)^2 (e_ij . v~_ij) e_ij,
+ *              F^R = sigma (1 - r) theta_ij / sqrt(dt) e_ij,
+ *              sigma^2 = 2 gamma kT, theta_ij a unit Gaussian drawn from
+ *              Philox4x32-10 with counter (min id, max id, step) so that
+ *              theta_ij = theta_ji;
+ *   - eqs. 6-8, Fig. 3a: bonded terms F^S (harmonic, modified Morse, and
+ *              standard Morse), several records per pair allowed;
+ *   - section "Design concept of CAMUS": cells of edge >= r_c rebuilt every
+ *              step, no neighbour list;
+ *   - Fig. 1:  Groot's modified velocity-Verlet,
+ *              r += dt v + dt^2/2 f; v~ = v + lambda dt f; f' = F(r, v~);
+ *              v += dt/2 (f + f').
+ *
+ * Conventions for every call:
+ *   - Positions, velocities and forces cross the ABI as host arrays of
+ *     n*3 doubles in bead-id order (row i = bead i), caller-allocated.
+ *   - All input arrays are caller-owned and copied during the call; the
+ *     library owns all device memory and the handle until dpd_destroy.
+ *   - Return value 0 (DPD_OK) or a negative DPD_E* code.  Device-side errors
+ *     (non-finite state, a device wait that gave up) are sticky on the
+ *     handle and reported by the next synchronising call.
+ *   - One handle must not be used from two host threads at once.  There is
+ *     no global state; handles are independent.
+ *   - dpd_step only enqueues work on the handle's stream; the calls marked
+ *     "synchronises" wait for it.
+ */
+#ifndef LIBDPD_DPD_H
+#define LIBDPD_DPD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define DPD_OK          0
+#define DPD_EINVAL     -1   /* bad argument: L < 3, n <= 0, bad bond, ...     */
+#define DPD_ENOMEM     -2   /* device or host allocation failed              */
+#define DPD_ECUDA      -3   /* a CUDA runtime call failed                    */
+#define DPD_EUNSTABLE  -4   /* a position, velocity or force became NaN/Inf  */
+#define DPD_ETIMEOUT   -5   /* a bounded device wait gave up                 */
+#define DPD_ENOSTATE   -6   /* dpd_step / dpd_get_state before dpd_set_state */
+
+/* ---- options ----------------------------------------------------------- */
+#define DPD_FP32        0   /* FP32 forces, cell-relative FP32 positions     */
+#define DPD_FP64        1   /* FP64 everywhere (absolute FP64 positions)     */
+#define DPD_NOISE_GAUSS   0 /* theta by Box-Muller (default)                 */
+#define DPD_NOISE_UNIFORM 1 /* theta = sqrt(3) (2u - 1)                      */
+
+#define DPD_BOND_HARMONIC    1  /* eq. 6: U = k/2 (r - r0)^2                  */
+#define DPD_BOND_MORSE_PAPER 2  /* eq. 7 with Fig. 3a's alpha: |F| =
+                                   2 k alpha e (1 - e), e = exp(-alpha|r-r0|),
+                                   towards the partner on both sides of r0,
+                                   U = k (1 - e)^2                            */
+#define DPD_BOND_MORSE       3  /* U = k [(1 - exp(-alpha (r - r0)))^2 - 1]   */
+
+typedef struct dpd_handle dpd_handle;          /* opaque, library-owned */
+
+typedef struct {
+    double L[3];          /* periodic box edges; each L >= 3 (cells of edge
+                             L/floor(L) >= r_c = 1, at least 3 per side)    */
+} dpd_box;
+
+typedef struct {
+    int32_t i, j;         /* bead ids, 0 <= i, j < n, i != j                */
+    int32_t kind;         /* DPD_BOND_*                                      */
+    int32_t pad;          /* ignored                                         */
+    double r0;            /* equilibrium distance r_e                        */
+    double k;             /* C (harmonic) or K_M / D (Morse kinds)           */
+    double alpha;         /* Morse width; ignored for harmonic               */
+} dpd_bond;
+
+typedef struct {
+    double lambda;        /* velocity-predictor factor of Fig. 1 (0.65)      */
+    uint64_t seed;        /* Philox key of the pair noise                    */
+    int32_t precision;    /* DPD_FP32 (default) or DPD_FP64                  */
+    int32_t noise;        /* DPD_NOISE_GAUSS (default) or DPD_NOISE_UNIFORM  */
+    int32_t sample_every; /* accumulate running means every k steps (0=off)  */
+    int32_t tile_cells;   /* pair-kernel home cells per block (0 = auto)     */
+    int32_t threads;      /* pair-kernel threads per block (0 = auto)        */
+    int32_t use_graph;    /* replay steps from a captured CUDA graph (1)     */
+    void *cuda_stream;    /* cudaStream_t to run on; NULL = own stream       */
+} dpd_options;
+
+/* Observables of the current state (dpd_observables).
+ * kT = sum v^2 / (3n - 3); pressures are (virial)/(3V):
+ * p_ideal = sum v^2/(3V), p_cons = sum_{i<j} r_ij.F^C_ij/(3V),
+ * p_bond = sum_bonds r_ij.F^S_ij/(3V), p_total = their sum. */
+typedef struct {
+    int64_t step;         /* evaluation counter of the current force         */
+    double momentum[3];   /* sum_i v_i (FP64 accumulation)                   */
+    double kT;
+    double p_total, p_ideal, p_cons, p_bond;
+    double e_pair;        /* sum_{i<j} a_ij (1 - r)^2 / 2                    */
+    double e_bond;        /* bond energies                                   */
+    double sum_v2;
+    double kT_mean, p_mean;   /* running means over sampled steps           */
+    int64_t n_samples;
+    int32_t status;       /* sticky device status, 0 or a DPD_E* code        */
+    int32_t pad;
+} dpd_obs;
+
+/* Fill *opt with the defaults (lambda 0.65, seed 0, FP32, Gaussian noise,
+ * sample_every 0, automatic tiles, graphs on, own stream). */
+void dpd_default_options(dpd_options *opt);
+
+/* Create a system (eq. 3-8 parameters).  types[n] in [0, ntypes);
+ * a_ij[ntypes*ntypes] symmetric, row-major; gamma >= 0, kT >= 0, dt > 0.
+ * bonds[nbonds] and morse[nmorse] are both lists of bonded records (any
+ * kind; the split only mirrors 1-2 vs 1-3/1-5 decks, as in Fig. 3b) and may
+ * be NULL when their count is 0.  opt may be NULL (defaults).
+ * On success *out is a new handle; the state must be set before stepping.
+ * Errors: DPD_EINVAL, DPD_ENOMEM, DPD_ECUDA. */
+int dpd_create(const dpd_box *box, int64_t n, const int32_t *types, int32_t ntypes,
+               const double *a_ij, double gamma, double kT, double dt,
+               const dpd_bond *bonds, int64_t nbonds, const dpd_bond *morse, int64_t nmorse,
+               const dpd_options *opt, dpd_handle **out);
+
+/* Set positions pos[n*3] and velocities vel[n*3] (bead-id order; positions
+ * are wrapped into the box) and the evaluation counter `step`, then
+ * evaluate the force f(step) at v~ = v (Fig. 1's starting force).
+ * Synchronises.  Errors: DPD_EINVAL (NULL arrays, or a non-finite value,
+ * detected on the device; the previous state is then lost), DPD_ECUDA. */
+int dpd_set_state(dpd_handle *h, const double *pos, const double *vel, int64_t step);
+
+/* Enqueue nsteps steps of Fig. 1 (nsteps >= 0).  Asynchronous with respect
+ * to the host.  Errors: DPD_ENOSTATE, DPD_EINVAL, DPD_ECUDA, or a sticky
+ * device error from earlier work. */
+int dpd_step(dpd_handle *h, int64_t nsteps);
+
+/* Copy the state to host arrays in bead-id order: pos[n*3] (wrapped into
+ * [0, L)), vel[n*3], force[n*3] (total force of the last evaluation) -- any
+ * of them may be NULL -- and the evaluation counter to *step (nullable).
+ * Synchronises.  Errors: DPD_ENOSTATE, DPD_ECUDA, DPD_EUNSTABLE. */
+int dpd_get_state(dpd_handle *h, double *pos, double *vel, double *force, int64_t *step);
+
+/* Observables of the current state (dpd_obs above).  Synchronises. */
+int dpd_observables(dpd_handle *h, dpd_obs *out);
+
+/* Unique-pair distance histogram of the current state: counts[nbins] of
+ * minimum-image distances in bins of width rmax/nbins, r < rmax.
+ * rmax must satisfy 2*ceil(rmax/h)+1 <= n_c in every dimension.
+ * Synchronises.  Errors: DPD_EINVAL, DPD_ENOSTATE, DPD_ECUDA. */
+int dpd_gr(dpd_handle *h, double rmax, int32_t nbins, uint64_t *counts);
+
+/* The cell division of the current state: key_by_id[n] = cell key
+ * (cz*ny + cy)*nx + cx of bead id; order[n] = bead id at each sorted slot
+ * (cells ascending, ids ascending inside a cell); cell_start[ncells+1].
+ * Any pointer may be NULL.  Synchronises. */
+int dpd_get_cells(dpd_handle *h, uint32_t *key_by_id, int64_t *order, int64_t *cell_start);
+
+/* Cells per dimension n_c = floor(L) (cell edge h = L / n_c). */
+int dpd_cell_dims(const dpd_handle *h, int64_t nc[3]);
+
+/* Wait for all enqueued work; report sticky device errors. */
+int dpd_sync(dpd_handle *h);
+
+/* Number of kernel launches the handle has enqueued so far. */
+int64_t dpd_launch_count(const dpd_handle *h);
+
+/* Phase timing with CUDA events on the handle's stream, for benchmarks.
+ * dpd_profile_begin(h, max_steps) arms events for the next max_steps steps
+ * (max_steps in [1, 100000]); steps beyond that are not timed.
+ * dpd_profile_end synchronises and returns, summed over the timed steps,
+ * ms[0] = position update + cell division (k_update .. k_gather),
+ * ms[1] = pair forces (k_pair), ms[2] = bonds + velocity update + sampled
+ * reductions, and *nsteps = the number of steps timed.  Errors: DPD_EINVAL,
+ * DPD_ECUDA. */
+int dpd_profile_begin(dpd_handle *h, int64_t max_steps);
+int dpd_profile_end(dpd_handle *h, double ms[3], int64_t *nsteps);
+
+/* Free the handle and its device memory (NULL is allowed). */
+int dpd_destroy(dpd_handle *h);
+
+/* Static string for a DPD_E* code. */
+const char *dpd_strerror(int code);
+
+/* Detail of the handle's last error (static or handle-owned string);
+ * with h == NULL, the detail of this thread's last failed dpd_create. */
+const char *dpd_last_error(const dpd_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

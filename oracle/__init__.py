@@ -83,6 +83,7 @@ def _load():
             lib.orc_theta.restype = C.c_double
             lib.orc_pair_force_one.argtypes = [P, P, P, C.c_int64, C.c_int64, C.c_int64, P]
             lib.orc_pair_forces.argtypes = [P, P, P, C.c_int64, C.c_int32, P, P]
+            lib.orc_pair_forces_subset.argtypes = [P, P, P, C.c_int64, P, C.c_int64, P]
             lib.orc_bond_forces.argtypes = [P, P, P, P]
             lib.orc_bond_one.argtypes = [C.c_int32, C.c_double, C.c_double, C.c_double, P, P, P]
             lib.orc_forces.argtypes = [P, P, P, C.c_int64, C.c_int32, P, P]
@@ -180,6 +181,19 @@ def pair_forces(sys: System, pos, vt, s, mode=MODE_BRUTE):
     if rc:
         raise RuntimeError("orc_pair_forces failed: %d" % rc)
     return f, t
+
+
+def pair_forces_subset(sys: System, pos, vt, s, idx):
+    """Pair forces on the beads idx only (brute force over all j != i)."""
+    pos = _f64(pos, sys.n)
+    vt = _f64(vt, sys.n)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    f = np.zeros((idx.size, 3))
+    rc = _load().orc_pair_forces_subset(sys.ref, _ptr(pos), _ptr(vt), int(s), _ptr(idx),
+                                        int(idx.size), _ptr(f))
+    if rc:
+        raise RuntimeError("orc_pair_forces_subset failed: %d" % rc)
+    return f
 
 
 def bond_forces(sys: System, pos):

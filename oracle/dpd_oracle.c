@@ -247,6 +247,26 @@ int orc_pair_forces(const orc_sys *sys, const double *pos, const double *vt, int
     return rc;
 }
 
+int orc_pair_forces_subset(const orc_sys *sys, const double *pos, const double *vt, int64_t s,
+                           const int64_t *idx, int64_t m, double *f) {
+    for (int64_t q = 0; q < m; ++q)
+        if (idx[q] < 0 || idx[q] >= sys->n) return -3;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < m; ++q) {
+        const int64_t i = idx[q];
+        double fi[3] = {0, 0, 0};
+        for (int64_t j = 0; j < sys->n; ++j) {
+            if (j == i) continue;
+            double F[3], wc, ep;
+            if (pair_core(sys, pos, vt, i, j, s, F, &wc, &ep)) {
+                fi[0] += F[0]; fi[1] += F[1]; fi[2] += F[2];
+            }
+        }
+        f[3 * q] = fi[0]; f[3 * q + 1] = fi[1]; f[3 * q + 2] = fi[2];
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Bonded terms, eqs. 6-8 and Fig. 3a.                                       */
 /* ------------------------------------------------------------------------ */

@@ -77,6 +77,10 @@ void orc_pair_force_one(const orc_sys *sys, const double *pos, const double *vt,
 /* Pair forces f[n*3] (overwritten).  mode 0 = brute force, 1 = cell list. */
 int orc_pair_forces(const orc_sys *sys, const double *pos, const double *vt,
                     int64_t s, int32_t mode, double *f, orc_terms *t);
+/* Pair forces on the m beads idx[] only (plain definition, all j != i);
+ * f[m*3] overwritten.  For spot checks of very large systems. */
+int orc_pair_forces_subset(const orc_sys *sys, const double *pos, const double *vt, int64_t s,
+                           const int64_t *idx, int64_t m, double *f);
 /* Bond forces added into f[n*3]. */
 int orc_bond_forces(const orc_sys *sys, const double *pos, double *f, orc_terms *t);
 /* Force and energy of one bond record on bead i (F_j = -F_i). */

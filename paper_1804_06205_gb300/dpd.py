@@ -1,0 +1,245 @@
+"""ctypes binding of libdpd (include/dpd.h): argument marshalling only.
+
+Every step of the DPD loop runs in the CUDA kernels of ``libdpd.so``; this
+module converts numpy arrays to the C ABI's plain pointers and raises on
+error codes.  Importing it loads the library and fails loudly if it has not
+been built (``python -m paper_1804_06205_gb300.build``); there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdpd.so")
+
+DPD_OK = 0
+DPD_EINVAL = -1
+DPD_ENOMEM = -2
+DPD_ECUDA = -3
+DPD_EUNSTABLE = -4
+DPD_ETIMEOUT = -5
+DPD_ENOSTATE = -6
+
+DPD_FP32 = 0
+DPD_FP64 = 1
+DPD_NOISE_GAUSS = 0
+DPD_NOISE_UNIFORM = 1
+
+EXPORTED = ("dpd_default_options", "dpd_create", "dpd_set_state", "dpd_step", "dpd_get_state",
+            "dpd_observables", "dpd_gr", "dpd_get_cells", "dpd_cell_dims", "dpd_sync",
+            "dpd_launch_count", "dpd_profile_begin", "dpd_profile_end", "dpd_destroy",
+            "dpd_strerror", "dpd_last_error")
+
+
+class dpd_box(C.Structure):
+    _fields_ = [("L", C.c_double * 3)]
+
+
+class dpd_bond(C.Structure):
+    _fields_ = [("i", C.c_int32), ("j", C.c_int32), ("kind", C.c_int32), ("pad", C.c_int32),
+                ("r0", C.c_double), ("k", C.c_double), ("alpha", C.c_double)]
+
+
+class dpd_options(C.Structure):
+    _fields_ = [("lambda_", C.c_double), ("seed", C.c_uint64), ("precision", C.c_int32),
+                ("noise", C.c_int32), ("sample_every", C.c_int32), ("tile_cells", C.c_int32),
+                ("threads", C.c_int32), ("use_graph", C.c_int32), ("cuda_stream", C.c_void_p)]
+
+
+class dpd_obs(C.Structure):
+    _fields_ = [("step", C.c_int64), ("momentum", C.c_double * 3), ("kT", C.c_double),
+                ("p_total", C.c_double), ("p_ideal", C.c_double), ("p_cons", C.c_double),
+                ("p_bond", C.c_double), ("e_pair", C.c_double), ("e_bond", C.c_double),
+                ("sum_v2", C.c_double), ("kT_mean", C.c_double), ("p_mean", C.c_double),
+                ("n_samples", C.c_int64), ("status", C.c_int32), ("pad", C.c_int32)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("momentum", "pad")}
+        d["momentum"] = list(self.momentum)
+        return d
+
+
+class DPDError(RuntimeError):
+    def __init__(self, code, where, detail=""):
+        self.code = code
+        super().__init__("%s failed: %d (%s) %s" % (where, code, strerror(code), detail))
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libdpd.so is not built at %s; run "
+                          "`python -m paper_1804_06205_gb300.build` (needs nvcc)" % LIB_PATH)
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    lib.dpd_default_options.argtypes = [P]
+    lib.dpd_default_options.restype = None
+    lib.dpd_create.argtypes = [P, C.c_int64, P, C.c_int32, P, C.c_double, C.c_double, C.c_double,
+                               P, C.c_int64, P, C.c_int64, P, P]
+    lib.dpd_set_state.argtypes = [P, P, P, C.c_int64]
+    lib.dpd_step.argtypes = [P, C.c_int64]
+    lib.dpd_get_state.argtypes = [P, P, P, P, P]
+    lib.dpd_observables.argtypes = [P, P]
+    lib.dpd_gr.argtypes = [P, C.c_double, C.c_int32, P]
+    lib.dpd_get_cells.argtypes = [P, P, P, P]
+    lib.dpd_cell_dims.argtypes = [P, P]
+    lib.dpd_sync.argtypes = [P]
+    lib.dpd_launch_count.argtypes = [P]
+    lib.dpd_launch_count.restype = C.c_int64
+    lib.dpd_profile_begin.argtypes = [P, C.c_int64]
+    lib.dpd_profile_end.argtypes = [P, P, P]
+    lib.dpd_destroy.argtypes = [P]
+    lib.dpd_strerror.argtypes = [C.c_int]
+    lib.dpd_strerror.restype = C.c_char_p
+    lib.dpd_last_error.argtypes = [P]
+    lib.dpd_last_error.restype = C.c_char_p
+    return lib
+
+
+lib = _load()
+
+
+def strerror(code):
+    return lib.dpd_strerror(int(code)).decode()
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def default_options(**kw) -> dpd_options:
+    o = dpd_options()
+    lib.dpd_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, "lambda_" if k in ("lam", "lambda") else k, v)
+    return o
+
+
+def _records_fast(b):
+    m = len(b["i"])
+    dt = np.dtype([("i", "<i4"), ("j", "<i4"), ("kind", "<i4"), ("pad", "<i4"), ("r0", "<f8"),
+                   ("k", "<f8"), ("alpha", "<f8")])
+    rec = np.zeros(max(m, 1), dtype=dt)
+    if m:
+        rec["i"], rec["j"], rec["kind"] = b["i"], b["j"], b["kind"]
+        rec["r0"], rec["k"], rec["alpha"] = b["r0"], b["k"], b["alpha"]
+    return rec, m
+
+
+class System:
+    """One DPD system owned by libdpd (a thin wrapper over the C handle)."""
+
+    def __init__(self, L, types, a, gamma, kT, dt, bonds=None, morse=None, options=None, **opt):
+        self.h = C.c_void_p()
+        L = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,))
+        box = dpd_box((C.c_double * 3)(*L))
+        self.types = np.ascontiguousarray(types, dtype=np.int32)
+        self.n = int(self.types.size)
+        self.a = np.ascontiguousarray(a, dtype=np.float64)
+        ntypes = int(round(np.sqrt(self.a.size)))
+        if options is None:
+            options = default_options(**opt)
+        self.options = options
+        empty = dict(i=[], j=[], kind=[], r0=[], k=[], alpha=[])
+        brec, nb = _records_fast(bonds if bonds is not None else empty)
+        mrec, nm = _records_fast(morse if morse is not None else empty)
+        self._keep = (brec, mrec)
+        rc = lib.dpd_create(C.byref(box), self.n, _ptr(self.types), ntypes, _ptr(self.a),
+                            float(gamma), float(kT), float(dt), _ptr(brec), nb, _ptr(mrec), nm,
+                            C.byref(options), C.byref(self.h))
+        if rc != DPD_OK:
+            raise DPDError(rc, "dpd_create", lib.dpd_last_error(None).decode())
+        nc = np.zeros(3, np.int64)
+        lib.dpd_cell_dims(self.h, _ptr(nc))
+        self.nc = nc
+        self.L = np.array(L)
+
+    @classmethod
+    def from_workload(cls, w, **opt):
+        opt.setdefault("seed", w.seed)
+        opt.setdefault("lam", w.lam)
+        return cls(w.L, w.types, w.a, w.gamma, w.kT, w.dt, bonds=w.bonds, **opt)
+
+    def _check(self, rc, where):
+        if rc != DPD_OK:
+            raise DPDError(rc, where, lib.dpd_last_error(self.h).decode())
+
+    def set_state(self, pos, vel, step=0):
+        pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(self.n, 3)
+        vel = np.ascontiguousarray(vel, dtype=np.float64).reshape(self.n, 3)
+        self._check(lib.dpd_set_state(self.h, _ptr(pos), _ptr(vel), int(step)), "dpd_set_state")
+
+    def set_state_ptr(self, pos_ptr, vel_ptr, step=0):
+        """Host pointers (e.g. of pinned buffers) of n*3 doubles each."""
+        self._check(lib.dpd_set_state(self.h, C.c_void_p(pos_ptr), C.c_void_p(vel_ptr), int(step)),
+                    "dpd_set_state")
+
+    def step(self, nsteps=1):
+        self._check(lib.dpd_step(self.h, int(nsteps)), "dpd_step")
+
+    def get_state(self, pos=True, vel=True, force=True):
+        out = [np.empty((self.n, 3)) if f else None for f in (pos, vel, force)]
+        st = C.c_int64(0)
+        self._check(lib.dpd_get_state(self.h, _ptr(out[0]), _ptr(out[1]), _ptr(out[2]),
+                                      C.byref(st)), "dpd_get_state")
+        return out[0], out[1], out[2], st.value
+
+    def get_state_ptr(self, pos_ptr=None, vel_ptr=None, force_ptr=None):
+        st = C.c_int64(0)
+        self._check(lib.dpd_get_state(self.h, C.c_void_p(pos_ptr), C.c_void_p(vel_ptr),
+                                      C.c_void_p(force_ptr), C.byref(st)), "dpd_get_state")
+        return st.value
+
+    def observables(self) -> dict:
+        o = dpd_obs()
+        self._check(lib.dpd_observables(self.h, C.byref(o)), "dpd_observables")
+        return o.as_dict()
+
+    def gr_counts(self, rmax, nbins):
+        c = np.zeros(nbins, dtype=np.uint64)
+        self._check(lib.dpd_gr(self.h, float(rmax), int(nbins), _ptr(c)), "dpd_gr")
+        return c
+
+    def cells(self):
+        key = np.zeros(self.n, np.uint32)
+        order = np.zeros(self.n, np.int64)
+        start = np.zeros(int(np.prod(self.nc)) + 1, np.int64)
+        self._check(lib.dpd_get_cells(self.h, _ptr(key), _ptr(order), _ptr(start)),
+                    "dpd_get_cells")
+        return key, order, start
+
+    def sync(self):
+        self._check(lib.dpd_sync(self.h), "dpd_sync")
+
+    def launch_count(self) -> int:
+        return int(lib.dpd_launch_count(self.h))
+
+    def profile_begin(self, max_steps):
+        self._check(lib.dpd_profile_begin(self.h, int(max_steps)), "dpd_profile_begin")
+
+    def profile_end(self):
+        """-> (ms per phase summed over timed steps [update+sort, pair, bond+v], steps)"""
+        ms = np.zeros(3)
+        n = C.c_int64(0)
+        self._check(lib.dpd_profile_end(self.h, _ptr(ms), C.byref(n)), "dpd_profile_end")
+        return ms, n.value
+
+    def close(self):
+        if self.h:
+            lib.dpd_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,345 @@
+"""GPU parity of the CUDA engine (through the C ABI) against the FP64 oracle.
+
+Tolerances (from the arithmetic of each path):
+  * cell keys, sort order, cell starts, g(r) counts of the FP64 path: bit-exact;
+  * one force evaluation from an identical state: max|f_gpu - f_oracle| <=
+    1e-4 max|f| for FP32 (FP32 pair arithmetic, ~1e-6 relative per pair,
+    summed over ~13 hits), 1e-10 max|f| for FP64 (summation order only);
+  * long-run statistics (kT, pressure) within 1%, g(r) within 0.01 absolute.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1804_06205_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP32, FP64 = 0, 1
+TOL = {FP32: 1e-4, FP64: 1e-10}
+
+
+@pytest.fixture(scope="module")
+def D():
+    from paper_1804_06205_gb300 import build
+    build.build()
+    from paper_1804_06205_gb300 import dpd
+    return dpd
+
+
+def osys(w, noise=0):
+    return O.System(w.L, w.types, w.a, w.gamma, w.kT, w.dt, w.lam, seed=w.seed, noise=noise,
+                    bonds=w.bonds)
+
+
+def gsys(D, w, prec, **kw):
+    return D.System.from_workload(w, precision=prec, **kw)
+
+
+def small_workloads():
+    melt = W.melt_98k(L=10.0, seed=21)
+    pep = W.peptide_192k(L=10.0, nchains=10, chain_len=20, seed=22)
+    helix = W.alpha_helix_24k()
+    helix_small = W.Workload("helix_small", np.array([8.0, 8.0, 8.0]),
+                             np.concatenate([helix.types[:60], np.ones(1476, np.int32)]),
+                             helix.a, helix.gamma, helix.kT, helix.dt, helix.lam, 23,
+                             np.concatenate([helix.pos[:60] % 8.0,
+                                             np.random.default_rng(2).uniform(0, 8, (1476, 3))]),
+                             W.maxwell_velocities(np.random.default_rng(3), 1536),
+                             helix.bonds)
+    odd = W.fluid((7.3, 9.1, 11.7), ntypes=3, a_same=25.0, a_cross=33.0, seed=24)
+    return {"fluid_3k": W.fluid_3k(), "melt": melt, "peptide": pep, "helix": helix_small,
+            "odd_box": odd}
+
+
+WL = small_workloads()
+
+
+# ------------------------------------------------------------------ cells
+def _oracle_cells(w, pos):
+    s = osys(w)
+    p = O.wrap(s, pos)
+    key = O.cell_keys(s, p)
+    order, start = O.cell_sort(s, key)
+    return key, order, start
+
+
+def _face_positions(L, n, seed):
+    """Positions with many exact cell faces, L - eps, 0 and out-of-box values."""
+    rng = np.random.default_rng(seed)
+    L = np.asarray(L, float)
+    nc = np.floor(L)
+    h = L / nc
+    pos = rng.uniform(0, 1, (n, 3)) * L
+    m = n // 4
+    pos[:m] = rng.integers(0, nc.astype(int), (m, 3)) * h          # on faces
+    pos[m:m + 10] = np.nextafter(L, 0)                               # L - eps
+    pos[m + 10:m + 20] = 0.0
+    pos[m + 20:m + 40] += L * rng.integers(-3, 4, (20, 3))           # unwrapped
+    pos[m + 40:m + 50] = -1e-18
+    return pos
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+@pytest.mark.parametrize("L", [(10.0, 10.0, 10.0), (7.3, 9.1, 11.7), (3.0, 4.5, 3.2)])
+def test_cells_bitexact_at_set_state(D, prec, L):
+    n = int(3 * np.prod(L))
+    w = W.fluid(L, n=n, seed=31)
+    pos = _face_positions(L, n, 32)
+    g = gsys(D, w, prec)
+    g.set_state(pos, w.vel, 0)
+    key, order, start = g.cells()
+    okey, oorder, ostart = _oracle_cells(w, pos)
+    assert np.array_equal(key, okey)
+    assert np.array_equal(order, oorder)
+    assert np.array_equal(start, ostart)
+
+
+def test_cells_bitexact_after_steps_fp64(D):
+    w = WL["melt"]
+    g = gsys(D, w, FP64)
+    g.set_state(w.pos, w.vel, 0)
+    g.step(25)
+    pos, _, _, step = g.get_state()
+    assert step == 25
+    key, order, start = g.cells()
+    okey, oorder, ostart = _oracle_cells(w, pos)
+    assert np.array_equal(key, okey)
+    assert np.array_equal(order, oorder)
+    assert np.array_equal(start, ostart)
+
+
+def test_cells_invariants_after_steps_fp32(D):
+    w = WL["odd_box"]
+    g = gsys(D, w, FP32)
+    g.set_state(w.pos, w.vel, 0)
+    g.step(25)
+    pos, _, _, _ = g.get_state()
+    key, order, start = g.cells()
+    nc = g.nc
+    assert sorted(order.tolist()) == list(range(w.n))
+    ks = key[order].astype(np.int64)
+    assert np.all(np.diff(ks) >= 0)
+    assert np.all(np.diff(order)[np.diff(ks) == 0] > 0)
+    assert np.array_equal(np.diff(start), np.bincount(key.astype(np.int64),
+                                                      minlength=int(np.prod(nc))))
+    # the key agrees with the oracle's key of the returned position except for
+    # beads within FP32 rounding of a cell face
+    okey = O.cell_keys(osys(w), pos)
+    h = w.L / nc
+    frac = pos / h - np.floor(pos / h)
+    near = np.any((frac < 1e-5) | (frac > 1 - 1e-5), axis=1)
+    assert np.array_equal(key[~near], okey[~near])
+
+
+# ------------------------------------------------------------------ forces
+@pytest.mark.parametrize("prec", [FP32, FP64])
+@pytest.mark.parametrize("name", sorted(WL))
+def test_one_force_evaluation_matches_oracle(D, prec, name):
+    w = WL[name]
+    g = gsys(D, w, prec)
+    g.set_state(w.pos, w.vel, 17)
+    _, _, f, step = g.get_state()
+    assert step == 17
+    fo, _ = O.forces(osys(w), O.wrap(osys(w), w.pos), w.vel, 17)
+    scale = np.abs(fo).max()
+    err = np.abs(f - fo).max()
+    assert err <= TOL[prec] * scale, (err, scale)
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_uniform_noise_option(D, prec):
+    w = WL["fluid_3k"]
+    g = gsys(D, w, prec, noise=D.DPD_NOISE_UNIFORM)
+    g.set_state(w.pos, w.vel, 3)
+    _, _, f, _ = g.get_state()
+    s = osys(w, noise=O.NOISE_UNIFORM)
+    fo, _ = O.forces(s, w.pos, w.vel, 3)
+    assert np.abs(f - fo).max() <= TOL[prec] * np.abs(fo).max()
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_one_step_matches_oracle(D, prec):
+    w = WL["peptide"]
+    g = gsys(D, w, prec)
+    g.set_state(w.pos, w.vel, 0)
+    g.step(1)
+    pos, vel, f, step = g.get_state()
+    st = O.State(osys(w), w.pos, w.vel, 0)
+    st.run(1)
+    assert step == st.step == 1
+    d = pos - st.pos
+    d -= w.L * np.round(d / w.L)
+    assert np.abs(d).max() < (1e-5 if prec == FP32 else 1e-12)
+    assert np.abs(vel - st.vel).max() <= TOL[prec] * np.abs(st.f).max()
+    assert np.abs(f - st.f).max() <= 2 * TOL[prec] * np.abs(st.f).max()
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_observables_match_oracle_at_identical_state(D, prec):
+    w = WL["peptide"]
+    g = gsys(D, w, prec)
+    g.set_state(w.pos, w.vel, 5)
+    o = g.observables()
+    st = O.State(osys(w), w.pos, w.vel, 5)
+    oo = st.observables()
+    tol = 1e-5 if prec == FP32 else 1e-10
+    for k in ("kT", "p_total", "p_ideal", "p_cons", "p_bond", "e_pair", "e_bond"):
+        assert abs(o[k] - oo[k]) <= tol * max(1.0, abs(oo[k])), (k, o[k], oo[k])
+    assert o["step"] == 5
+
+
+# ------------------------------------------------------------------ invariants
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_momentum_conserved_and_runs_deterministic(D, prec):
+    w = WL["melt"]
+    runs = []
+    for _ in range(2):
+        g = gsys(D, w, prec)
+        g.set_state(w.pos, w.vel, 0)
+        g.step(60)
+        runs.append(g.get_state())
+        g.close()
+    for a, b in zip(runs[0][:3], runs[1][:3]):
+        assert np.array_equal(a, b)
+    p = runs[0][1].sum(axis=0)
+    assert np.abs(p).max() < (2e-3 if prec == FP32 else 1e-10)
+
+
+def test_results_do_not_depend_on_tiling_or_graphs(D):
+    w = WL["odd_box"]
+    ref = None
+    for opt in (dict(), dict(tile_cells=3, threads=64), dict(tile_cells=12, threads=256),
+                dict(use_graph=0), dict(tile_cells=1, threads=128, use_graph=0)):
+        g = gsys(D, w, FP32, **opt)
+        g.set_state(w.pos, w.vel, 0)
+        g.step(7)
+        out = g.get_state()
+        g.close()
+        if ref is None:
+            ref = out
+        else:
+            for a, b in zip(ref[:3], out[:3]):
+                assert np.array_equal(a, b), opt
+
+
+def test_gr_counts_fp64_bitexact(D):
+    w = WL["fluid_3k"]
+    g = gsys(D, w, FP64)
+    g.set_state(w.pos, w.vel, 0)
+    c = g.gr_counts(3.0, 150)
+    co = O.gr_counts(osys(w), O.wrap(osys(w), w.pos), 3.0, 150)
+    assert np.array_equal(c, co)
+
+
+# ------------------------------------------------------------------ edge cases
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_edge_single_bead_and_pair(D, prec):
+    w1 = W.fluid(4.0, n=1, seed=3)
+    g = gsys(D, w1, prec)
+    g.set_state(w1.pos, w1.vel, 0)
+    g.step(3)
+    _, v, f, _ = g.get_state()
+    assert np.all(f == 0.0) and np.allclose(v, w1.vel)
+    w2 = W.fluid(4.0, n=2, seed=4)
+    w2.pos[:] = [[0.05, 2.0, 2.0], [3.7, 2.1, 1.9]]    # a pair across the boundary
+    g = gsys(D, w2, prec)
+    g.set_state(w2.pos, w2.vel, 9)
+    _, _, f, _ = g.get_state()
+    fo, _ = O.forces(osys(w2), w2.pos, w2.vel, 9)
+    assert np.abs(f - fo).max() <= TOL[prec] * np.abs(fo).max()
+    assert np.abs(fo).max() > 0
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_edge_crowded_cell_uses_chunks_and_passes(D, prec):
+    # 600 beads inside one cell of a 5^3 box plus a sparse background: the
+    # neighbourhood exceeds the staged capacity and every bead has ~600 hits
+    rng = np.random.default_rng(5)
+    n = 900
+    w = W.fluid(5.0, n=n, seed=6)
+    w.pos[:600] = 2.0 + rng.uniform(0, 0.9, (600, 3))
+    g = gsys(D, w, prec)
+    g.set_state(w.pos, w.vel, 4)
+    _, _, f, _ = g.get_state()
+    fo, _ = O.forces(osys(w), w.pos, w.vel, 4)
+    assert np.abs(f - fo).max() <= TOL[prec] * np.abs(fo).max()
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_edge_smallest_box(D, prec):
+    w = W.fluid(3.0, n=81, seed=8)
+    g = gsys(D, w, prec)
+    g.set_state(w.pos, w.vel, 2)
+    _, _, f, _ = g.get_state()
+    fo, _ = O.forces(osys(w), w.pos, w.vel, 2)
+    assert np.abs(f - fo).max() <= TOL[prec] * np.abs(fo).max()
+
+
+def test_errors_are_reported(D):
+    w = WL["fluid_3k"]
+    g = gsys(D, w, FP32)
+    with pytest.raises(D.DPDError) as e:
+        g.step(1)
+    assert e.value.code == D.DPD_ENOSTATE
+    bad = w.pos.copy()
+    bad[7, 1] = np.nan
+    with pytest.raises(D.DPDError) as e:
+        g.set_state(bad, w.vel, 0)
+    assert e.value.code == D.DPD_EINVAL
+
+
+# ------------------------------------------------------------------ long run
+def test_long_run_statistics_match_oracle(D):
+    """fluid_3k, 1000 steps: kT and pressure within 1%, g(r) within 0.01."""
+    w = WL["fluid_3k"]
+    nb, rmax = 60, 3.0
+    g = gsys(D, w, FP32)
+    g.set_state(w.pos, w.vel, 0)
+    g.step(200)
+    gk, gp, gcnt = [], [], np.zeros(nb)
+    for _ in range(80):
+        g.step(10)
+        o = g.observables()
+        gk.append(o["kT"])
+        gp.append(o["p_total"])
+        gcnt += g.gr_counts(rmax, nb)
+    s = osys(w)
+    st = O.State(s, w.pos, w.vel, 0, mode=O.MODE_CELLS)
+    st.run(200)
+    ok, op, ocnt = [], [], np.zeros(nb)
+    for _ in range(80):
+        smp = st.run(10, sample_every=10)
+        ok.append(smp[-1, 4])
+        op.append(smp[-1, 5])
+        ocnt += O.gr_counts(s, st.pos, rmax, nb)
+    assert abs(np.mean(gk) - np.mean(ok)) < 0.01 * np.mean(ok)
+    assert abs(np.mean(gp) - np.mean(op)) < 0.01 * np.mean(op)
+    gg = O.gr_normalise(gcnt / 80, w.n, w.L, rmax)
+    go = O.gr_normalise(ocnt / 80, w.n, w.L, rmax)
+    r = (np.arange(nb) + 0.5) * rmax / nb
+    m = r >= 0.1
+    assert np.abs(gg[m] - go[m]).max() < 0.01
+
+
+# ------------------------------------------------------------------ full size
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_full_size_fluid_3m_sampled_parity(D, prec):
+    """The 100^3, N = 3,000,000 fluid in the benchmark's launch configuration
+    (default options): cells bit-exact for all beads, forces on 256 sampled
+    beads against the oracle's brute-force sum, total force ~ 0."""
+    w = W.fluid_3m()
+    g = gsys(D, w, prec)
+    g.set_state(w.pos, w.vel, 11)
+    _, _, f, _ = g.get_state()
+    key, order, start = g.cells()
+    okey, oorder, ostart = _oracle_cells(w, w.pos)
+    assert np.array_equal(key, okey)
+    assert np.array_equal(order, oorder)
+    assert np.array_equal(start, ostart)
+    idx = np.random.default_rng(12).choice(w.n, 256, replace=False)
+    s = osys(w)
+    fo = O.pair_forces_subset(s, w.pos, w.vel, 11, idx)
+    scale = np.abs(fo).max()
+    assert np.abs(f[idx] - fo).max() <= TOL[prec] * scale
+    assert np.abs(f.sum(axis=0)).max() < (1e-2 if prec == FP32 else 1e-6) * np.sqrt(w.n)

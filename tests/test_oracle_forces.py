@@ -186,3 +186,12 @@ def test_bond_forces_antisymmetric_through_boundary():
     F02, _ = O.bond_one(3, 0.7, 5.0, 3.0, pos[0] - pos[2])
     assert np.allclose(f[0], F01 + F02, atol=1e-13)
     assert np.allclose(f[1], -F01, atol=1e-13)
+
+
+def test_subset_forces_equal_full_rows():
+    w = W.fluid(6.0, n=700, ntypes=2, a_cross=35.0, seed=4)
+    s = O.System(w.L, w.types, w.a, w.gamma, w.kT, w.dt, seed=5)
+    f, _ = O.pair_forces(s, w.pos, w.vel, 3)
+    idx = np.array([0, 5, 699, 350, 5])
+    fs = O.pair_forces_subset(s, w.pos, w.vel, 3, idx)
+    assert np.array_equal(fs, f[idx])
