@@ -335,7 +335,8 @@ class Engine : public EngineBase {
     // while a graph is captured, a timing event when profiling direct launches.
     int mark(int k, bool capturing) {
         if (capturing) {
-            DPD_CU(cudaEventRecord(ph_[k], stream_));
+            // "external" so that the capture turns it into an event-record node
+            DPD_CU(cudaEventRecordWithFlags(ph_[k], stream_, cudaEventRecordExternal));
         } else if (prof_on_ && prof_n_ < prof_max_) {
             DPD_CU(cudaEventRecord(prof_ev_[4 * prof_n_ + k], stream_));
             if (k == 3) ++prof_n_;
