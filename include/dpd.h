@@ -180,6 +180,33 @@ int64_t dpd_launch_count(const dpd_handle *h);
 int dpd_profile_begin(dpd_handle *h, int64_t max_steps);
 int dpd_profile_end(dpd_handle *h, double ms[3], int64_t *nsteps);
 
+/* Cell division without any allocation.  The paper has no counterpart: it
+ * exists for callers that cannot call cudaMalloc -- code whose device memory
+ * belongs to a framework allocator or a fixed, pre-budgeted arena, and code
+ * that must avoid cudaMalloc's implicit device synchronisation.
+ * Computes, for n positions already in device memory, exactly what
+ * dpd_set_state + dpd_get_cells give: the periodic wrap into [0, L), the cell
+ * key (cz*ny + cy)*nx + cx with n_c = floor(L), and the canonical (cell, id)
+ * order.  All buffers are the caller's device memory:
+ *   pos_dev[n*3]            input, FP64, bead-id order;
+ *   key_dev[n]              output, cell key of each bead id;
+ *   order_dev[n]            output, bead id at each sorted slot;
+ *   cell_start_dev[ncell+1] output, first slot of each cell (also used as the
+ *                           count array, so it is cleared by the call).
+ * The work is enqueued on cuda_stream (NULL = the legacy default stream) and
+ * the call returns without waiting.  Scratch lives in one fixed array inside
+ * the library (16 MiB + 8 KiB per GPU that loads it, held until exit), shared by
+ * all calls and keeping the last call's contents: calls that overlap on the
+ * GPU race.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make it before any stream capture.
+ * Errors: DPD_EINVAL for NULL pointers, a box edge < 3, n outside
+ * [1, DPD_NOALLOC_MAX_N] or more than DPD_NOALLOC_MAX_CELLS cells;
+ * DPD_ECUDA if the address lookup or a launch fails. */
+#define DPD_NOALLOC_MAX_N     4194304
+#define DPD_NOALLOC_MAX_CELLS 4194304
+int dpd_cells_noalloc(const double *pos_dev, int64_t n, const dpd_box *box, uint32_t *key_dev,
+                      int32_t *order_dev, uint32_t *cell_start_dev, void *cuda_stream);
+
 /* Free the handle and its device memory (NULL is allowed). */
 int dpd_destroy(dpd_handle *h);
 

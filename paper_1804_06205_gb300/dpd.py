@@ -32,7 +32,7 @@ DPD_NOISE_UNIFORM = 1
 EXPORTED = ("dpd_default_options", "dpd_create", "dpd_set_state", "dpd_step", "dpd_get_state",
             "dpd_observables", "dpd_gr", "dpd_get_cells", "dpd_cell_dims", "dpd_sync",
             "dpd_launch_count", "dpd_profile_begin", "dpd_profile_end", "dpd_destroy",
-            "dpd_strerror", "dpd_last_error")
+            "dpd_strerror", "dpd_last_error", "dpd_cells_noalloc")
 
 
 class dpd_box(C.Structure):
@@ -96,6 +96,7 @@ def _load():
     lib.dpd_strerror.restype = C.c_char_p
     lib.dpd_last_error.argtypes = [P]
     lib.dpd_last_error.restype = C.c_char_p
+    lib.dpd_cells_noalloc.argtypes = [P, C.c_int64, P, P, P, P, P]
     return lib
 
 
@@ -108,6 +109,21 @@ def strerror(code):
 
 def _ptr(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+NOALLOC_MAX_N = 4194304
+NOALLOC_MAX_CELLS = 4194304
+
+
+def cells_noalloc(pos_dev_ptr, n, L, key_dev_ptr, order_dev_ptr, cell_start_dev_ptr,
+                  stream_ptr=None):
+    """dpd_cells_noalloc on caller-owned device buffers (raw pointers); returns
+    the DPD_* code.  Enqueued on the stream; the caller synchronises."""
+    L = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,))
+    box = dpd_box((C.c_double * 3)(*L))
+    return lib.dpd_cells_noalloc(C.c_void_p(pos_dev_ptr), int(n), C.byref(box),
+                                 C.c_void_p(key_dev_ptr), C.c_void_p(order_dev_ptr),
+                                 C.c_void_p(cell_start_dev_ptr), C.c_void_p(stream_ptr))
 
 
 def default_options(**kw) -> dpd_options:
