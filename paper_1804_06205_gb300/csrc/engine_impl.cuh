@@ -391,25 +391,41 @@ class Engine : public EngineBase {
     }
 
     void choose_tiles() {
-        // threads per block and home cells per block: about 0.8 T home beads
+        // threads per block; bricks of X x 2 x 2 cells holding about 0.85 T beads
         T_ = cfg_.threads > 0 ? cfg_.threads : 128;
         if (T_ != 64 && T_ != 128 && T_ != 256) T_ = 128;
+        BY_ = std::min(2, geo_.ny);
+        BZ_ = std::min(2, geo_.nz);
         const double per_cell = (double)n_ / (double)geo_.ncell;
-        int xmax = cfg_.tile_cells > 0 ? cfg_.tile_cells
-                                       : (int)std::floor(0.8 * T_ / std::max(per_cell, 0.25));
+        int xmax = cfg_.tile_cells > 0
+                       ? cfg_.tile_cells
+                       : (int)std::floor(0.85 * T_ / (BY_ * BZ_ * std::max(per_cell, 0.25)));
         xmax = std::max(1, std::min(xmax, PAIR_MAXX));
-        const int segs = (geo_.nx + xmax - 1) / xmax;
-        X_ = (geo_.nx + segs - 1) / segs;
-        segs_per_row_ = (geo_.nx + X_ - 1) / X_;
-        nseg_ = segs_per_row_ * geo_.ny * geo_.nz;
-        hmax_ = 32;
-        // staged capacity: the mean 9 (X+2) cells plus ~6 sigma, within 100 KB
-        const double mean = 9.0 * (X_ + 2) * per_cell;
-        int cap = (int)std::ceil(mean + 6.0 * std::sqrt(mean) + 32.0);
+        X_ = xmax;
+        if (cfg_.tile_cells <= 0) {   // the length near xmax that wastes the fewest cells
+            int best = xmax, waste = 1 << 30;
+            for (int x = std::max(1, xmax - 2); x <= std::min(PAIR_MAXX, xmax + 1); ++x) {
+                const int w = ((geo_.nx + x - 1) / x) * x - geo_.nx;
+                if (w < waste) {
+                    waste = w;
+                    best = x;
+                }
+            }
+            X_ = best;
+        }
+        X_ = std::min(X_, geo_.nx);
+        nbx_ = (geo_.nx + X_ - 1) / X_;
+        nby_ = (geo_.ny + BY_ - 1) / BY_;
+        nbz_ = (geo_.nz + BZ_ - 1) / BZ_;
+        nseg_ = nbx_ * nby_ * nbz_;
+        // staged capacity: the mean of (BY+2)(BZ+2)(X+2) cells plus ~4 sigma;
+        // larger neighbourhoods are staged in chunks (slots must fit 11 bits)
+        const double mean = (BY_ + 2) * (BZ_ + 2) * (X_ + 2) * per_cell;
+        int cap = (int)std::ceil(mean + 4.0 * std::sqrt(mean) + 32.0);
         cap = (cap + 31) / 32 * 32;
-        const int cap_max = (int)((100 * 1024) / (2 * sizeof(vec4)));
+        const int cap_max = (int)((96 * 1024) / (2 * sizeof(vec4)));
         cap_ = std::max(64, std::min(cap, std::min(cap_max, 2016)));
-        smem_ = PairSmem<P>::bytes(cap_, X_, T_, hmax_);
+        smem_ = PairSmem<P>::bytes(cap_, X_, T_);
     }
 
     // dynamic shared memory above the 48 KB default, set once (not while a
@@ -463,19 +479,25 @@ class Engine : public EngineBase {
         pa.ny = geo_.ny;
         pa.nz = geo_.nz;
         pa.X = X_;
-        pa.segs_per_row = segs_per_row_;
-        for (int k = 0; k < 3; ++k) {
-            pa.h[k] = (real)geo_.h[k];
-            pa.L[k] = (real)geo_.L[k];
-        }
+        pa.BY = BY_;
+        pa.BZ = BZ_;
+        pa.nbx = nbx_;
+        pa.nby = nby_;
+        for (int k = 0; k < 3; ++k) pa.h[k] = (real)geo_.h[k];
         pa.gamma = (real)cfg_.gamma;
         pa.sig_sqdt = (real)(std::sqrt(2.0 * cfg_.gamma * cfg_.kT) / std::sqrt(cfg_.dt));
-        pa.key0 = (uint32_t)(cfg_.seed & 0xffffffffull);
-        pa.key1 = (uint32_t)(cfg_.seed >> 32);
+        {   // Philox round keys: (k0, k1) + r (0x9E3779B9, 0xBB67AE85)
+            uint32_t k0 = (uint32_t)(cfg_.seed & 0xffffffffull), k1 = (uint32_t)(cfg_.seed >> 32);
+            for (int r = 0; r < 10; ++r) {
+                pa.rk[2 * r] = k0;
+                pa.rk[2 * r + 1] = k1;
+                k0 += 0x9E3779B9u;
+                k1 += 0xBB67AE85u;
+            }
+        }
         pa.noise = cfg_.noise;
         pa.counter = counter_;
         pa.cap = cap_;
-        pa.hmax = hmax_;
         switch (T_) {
             case 64: return sample ? launch_pair_t<64, true>(pa) : launch_pair_t<64, false>(pa);
             case 256: return sample ? launch_pair_t<256, true>(pa) : launch_pair_t<256, false>(pa);
@@ -567,6 +589,10 @@ class Engine : public EngineBase {
         ua.g = geo_;
         ua.dt = (real)cfg_.dt;
         ua.half_dt2 = (real)(0.5 * cfg_.dt * cfg_.dt);
+        for (int k = 0; k < 3; ++k) {
+            ua.hf[k] = (float)geo_.h[k];
+            ua.inv_hf[k] = (float)geo_.inv_h[k];
+        }
         ua.key = key_;
         ua.pos = pos_;
         ua.vel = vel_[cur_];
@@ -666,7 +692,7 @@ class Engine : public EngineBase {
     int64_t host_step_ = 0;
     int64_t launches_ = 0;
     int status_host_ = 0;
-    int T_ = 128, X_ = 1, segs_per_row_ = 1, nseg_ = 1, cap_ = 256, hmax_ = 32;
+    int T_ = 128, X_ = 1, BY_ = 2, BZ_ = 2, nbx_ = 1, nby_ = 1, nbz_ = 1, nseg_ = 1, cap_ = 256;
     size_t smem_ = 0;
     GraphSlot graphs_[2][3];
     cudaEvent_t ph_[4] = {nullptr, nullptr, nullptr, nullptr};

@@ -127,6 +127,19 @@ __device__ __forceinline__ double wrap_exact(double x, double L) {
     if (y >= L) y = __dsub_rn(y, L);
     return y;
 }
+// The same value as wrap_exact without a division, for x in [-L, 2L): there
+// x/L rounds to a q in {-1, 0, 1, 2} whose x - L q is exact or x + L, and the
+// two fix-ups map every such case onto x, x - L or x + L, as below.
+__device__ __forceinline__ double wrap_fast(double x, double L) {
+    if (!(x >= -L && x < 2.0 * L)) return wrap_exact(x, L);
+    double y = x;
+    if (y < 0.0) y = __dadd_rn(y, L);
+    else if (y >= L) y = __dsub_rn(y, L);
+    if (y < 0.0) y = __dadd_rn(y, L);
+    if (y >= L) y = __dsub_rn(y, L);
+    return y;
+}
+
 __device__ __forceinline__ int cell_of(double x, double inv_h, int n) {
     const double q = floor(__dmul_rn(x, inv_h));
     return (q > 0.0) ? (q < (double)(n - 1) ? (int)q : n - 1) : 0;   // NaN -> 0
@@ -154,6 +167,7 @@ struct UpdArgs {
     int n;
     Geo g;
     real dt, half_dt2;
+    float hf[3], inv_hf[3];   // cell edges in FP32 (offset path)
     const uint32_t *key;
     const vec4 *pos, *vel, *frc;
     vec4 *pos_tmp;
@@ -168,9 +182,9 @@ __device__ __forceinline__ void place_bead(const Geo &g, double x, double y, dou
                                            uint32_t &key, int *status, int bad_bit) {
     using real = typename P::real;
     if (!(isfinite(x) && isfinite(y) && isfinite(z))) atomicOr(status, bad_bit);
-    x = wrap_exact(x, g.L[0]);
-    y = wrap_exact(y, g.L[1]);
-    z = wrap_exact(z, g.L[2]);
+    x = wrap_fast(x, g.L[0]);
+    y = wrap_fast(y, g.L[1]);
+    z = wrap_fast(z, g.L[2]);
     const int cx = cell_of(x, g.inv_h[0], g.nx);
     const int cy = cell_of(y, g.inv_h[1], g.ny);
     const int cz = cell_of(z, g.inv_h[2], g.nz);
@@ -184,6 +198,24 @@ __device__ __forceinline__ void place_bead(const Geo &g, double x, double y, dou
     }
 }
 
+// FP32 path: the offset moves by the FP32 displacement and whole cells move
+// to the integer cell index, wrapped periodically -- the absolute position is
+// never formed.  FP64 path: x + displacement, wrapped in FP64.
+__device__ __forceinline__ int move_cell(float &o, float h, float inv_h, int c, int n) {
+    int d = (int)floorf(o * inv_h);
+    o = fmaf(-(float)d, h, o);
+    if (o < 0.0f) {
+        o += h;
+        --d;
+    }
+    if (o >= h) {
+        o -= h;
+        ++d;
+    }
+    int cc = (c + d) % n;
+    return cc < 0 ? cc + n : cc;
+}
+
 template <class P>
 __global__ void __launch_bounds__(256) k_update(UpdArgs<P> a) {
     using real = typename P::real;
@@ -194,20 +226,25 @@ __global__ void __launch_bounds__(256) k_update(UpdArgs<P> a) {
     const real ddx = a.dt * v.x + a.half_dt2 * f.x;
     const real ddy = a.dt * v.y + a.half_dt2 * f.y;
     const real ddz = a.dt * v.z + a.half_dt2 * f.z;
-    double x, y, z;
+    typename P::vec4 out;
+    uint32_t key;
     if (P::kOffsets) {
         int cx, cy, cz;
         decode_key(a.key[t], a.g, cx, cy, cz);
-        x = (double)cx * a.g.h[0] + (double)p.x;
-        y = (double)cy * a.g.h[1] + (double)p.y;
-        z = (double)cz * a.g.h[2] + (double)p.z;
+        float ox = (float)p.x + (float)ddx, oy = (float)p.y + (float)ddy, oz = (float)p.z + (float)ddz;
+        if (!(isfinite(ox) && isfinite(oy) && isfinite(oz))) {
+            atomicOr(a.status, ST_NONFINITE);
+            ox = oy = oz = 0.0f;
+        }
+        cx = move_cell(ox, a.hf[0], a.inv_hf[0], cx, a.g.nx);
+        cy = move_cell(oy, a.hf[1], a.inv_hf[1], cy, a.g.ny);
+        cz = move_cell(oz, a.hf[2], a.inv_hf[2], cz, a.g.nz);
+        key = ((uint32_t)cz * (uint32_t)a.g.ny + (uint32_t)cy) * (uint32_t)a.g.nx + (uint32_t)cx;
+        out = mk4<typename P::vec4, real>((real)ox, (real)oy, (real)oz, p.w);
     } else {
-        x = (double)p.x; y = (double)p.y; z = (double)p.z;
+        place_bead<P>(a.g, (double)p.x + (double)ddx, (double)p.y + (double)ddy,
+                      (double)p.z + (double)ddz, p.w, out, key, a.status, ST_NONFINITE);
     }
-    typename P::vec4 out;
-    uint32_t key;
-    place_bead<P>(a.g, x + (double)ddx, y + (double)ddy, z + (double)ddz, p.w, out, key, a.status,
-                  ST_NONFINITE);
     a.pos_tmp[t] = out;
     a.key_tmp[t] = key;
     a.rank[t] = atomicAdd(&a.count[key], 1u);
@@ -395,16 +432,29 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs<P> a) {
 }
 
 // --------------------------------------------------------------------------
-// a4-a5: pair forces, 27-cell full shell (each bead summed by one thread, no
-// force atomics).  A block owns a run of X consecutive cells of one x-row.
-// It stages the 9 neighbouring row runs (X+2 cells each, periodic) into
-// shared memory, then every thread takes one home bead: it walks the 27
-// neighbour cells in fixed (dz, dy, dx) order, collects the hits r < 1 in a
-// per-thread list and evaluates them in that order.  The neighbour cell's
-// periodic shift is applied to the home bead once per cell, so the staged
-// records are raw copies and a bead's sum does not depend on the tiling.
-// Oversized neighbourhoods are staged in chunks and long hit lists are
-// evaluated in passes; both keep the summation order.
+// a4-a5: pair forces, 27-cell full shell: every bead's force is summed in a
+// fixed order by its own warp, with no force atomics.
+//
+// A block owns a brick of X x BY x BZ home cells (BY, BZ <= 2).  It stages the
+// (BY+2)(BZ+2) neighbouring x-row runs (X+2 cells each, periodic) into shared
+// memory -- positions in the brick's frame (cell index relative to the
+// brick, times h, plus the offset; FP64: the absolute position moved by the
+// run's periodic image) and v~.  A home bead's 27 neighbour cells are 9 rows
+// of 3 consecutive staged cells; a row, or its first or last cell, is skipped
+// when its box lies at least r_c from the bead.
+//
+// Each warp takes 32 home beads (one per lane) and alternates two phases:
+//   scan     every lane records its hits r^2 < 1 in row and slot order, at
+//            most PAIR_HMAX per pass;
+//   evaluate the lists are compacted level by level (all first hits, then
+//            all second hits, ...) and evaluated 32 at a time, one hit per
+//            lane; each owner appears at most once per level, so the owners'
+//            sums in shared memory are updated level by level without
+//            conflicts, every owner adding its own hits in its own order.
+// Passes repeat until all 27 cells are done; oversized neighbourhoods are
+// staged in chunks.  Each bead's force is summed in a fixed order, so runs
+// are deterministic; another brick shape changes only the rounding of the
+// frame coordinates.
 // --------------------------------------------------------------------------
 template <class P>
 struct PairArgs {
@@ -416,236 +466,391 @@ struct PairArgs {
     const real *a;
     int ntypes;
     int nx, ny, nz;
-    int X, segs_per_row;
-    real h[3], L[3];
+    int X, BY, BZ, nbx, nby;          // brick shape, bricks along x and y
+    real h[3];
     real gamma, sig_sqdt;
-    uint32_t key0, key1;
+    uint32_t rk[20];                  // Philox round keys k + r (W0, W1)
     int noise;
     const long long *counter;
-    int cap, hmax;
+    int cap;
 };
 
-constexpr int PAIR_MAXX = 64;          // largest tile (cells per block)
+constexpr int PAIR_MAXX = 64;          // largest brick length (cells)
 constexpr int PAIR_MAXT = 16;          // largest number of bead types
+constexpr int PAIR_HMAX = 16;          // hits per lane per pass
+constexpr int PAIR_NR = 16;            // staged rows, (2+2) x (2+2)
+constexpr int PAIR_PC = 6;             // ints per staged run
 
 template <class P>
 struct PairSmem {
-    static size_t bytes(int cap, int X, int T, int hmax) {
-        size_t b = 2 * (size_t)cap * sizeof(typename P::vec4);
-        b += 9 * (size_t)(X + 3) * sizeof(int);
-        b += 27 * 3 * sizeof(int);
-        b = (b + 15) & ~(size_t)15;
-        b += PAIR_MAXT * PAIR_MAXT * sizeof(typename P::real);
-        b += (size_t)hmax * T * sizeof(uint16_t);
+    static __host__ __device__ size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+    static size_t bytes(int cap, int X, int T) {
+        using real = typename P::real;
+        using vec4 = typename P::vec4;
+        size_t b = 2 * (size_t)cap * sizeof(vec4);                 // staged positions, v~
+        b += PAIR_NR * (size_t)(X + 3) * sizeof(int);              // staged cell starts
+        b += PAIR_NR * 3 * PAIR_PC * sizeof(int) + 4 * 4 * sizeof(int);   // runs, home rows
+        b = align16(b);
+        b += PAIR_MAXT * PAIR_MAXT * sizeof(real) + PAIR_NR * 2 * sizeof(real);
+        b = align16(b);
+        const size_t nw = (size_t)T / 32;
+        b += nw * 32 * 2 * sizeof(vec4);                           // home beads (pos, v~)
+        b += nw * 32 * sizeof(vec4) + nw * 32 * sizeof(real);      // owners' sums
+        b += nw * PAIR_HMAX * 32 * sizeof(uint32_t);               // hit queue
         return b;
     }
 };
 
-template <class P>
-__device__ __forceinline__ void cell_shift(const PairArgs<P> &a, int ci, int cx, int cy, int cz,
-                                           typename P::real &sx, typename P::real &sy,
-                                           typename P::real &sz) {
-    using real = typename P::real;
-    const int rr = ci / 3;
-    const int ddx = ci - 3 * rr - 1, ddy = rr % 3 - 1, ddz = rr / 3 - 1;
-    if (P::kOffsets) {
-        // home-bead offset minus the neighbour cell's origin relative to its own cell
-        sx = -(real)ddx * a.h[0];
-        sy = -(real)ddy * a.h[1];
-        sz = -(real)ddz * a.h[2];
-    } else {
-        // absolute coordinates: undo the periodic wrap of the neighbour cell
-        const int ux = cx + ddx, uy = cy + ddy, uz = cz + ddz;
-        sx = ux < 0 ? a.L[0] : (ux >= a.nx ? -a.L[0] : (real)0);
-        sy = uy < 0 ? a.L[1] : (uy >= a.ny ? -a.L[1] : (real)0);
-        sz = uz < 0 ? a.L[2] : (uz >= a.nz ? -a.L[2] : (real)0);
+// Philox4x32-10 with precomputed round keys (outputs 0 and 1).
+__device__ __forceinline__ uint2 philox_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                           const uint32_t *rk) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk[2 * r];
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk[2 * r + 1];
+        c0 = n0; c1 = (uint32_t)p1; c2 = n2; c3 = (uint32_t)p0;
     }
+    return make_uint2(c0, c1);
+}
+
+// Box-Muller with the fast intrinsics (FP32 path): -2 ln u0 = -2 ln2 log2 u0,
+// cos(2 pi u1) = -cos(2 pi u1 - pi) with the argument in (-pi, pi).
+__device__ __forceinline__ float theta_pair(uint2 x, int noise, float) {
+    const float u0 = u01_f32(x.x);
+    if (noise) return 1.7320508075688772f * (2.0f * u0 - 1.0f);
+    const float u1 = u01_f32(x.y);
+    const float q = fmaxf(-1.3862943611198906f * __log2f(u0), 0.0f);
+    const float s = q > 0.0f ? q * rsqrtf(q) : 0.0f;
+    return -s * __cosf(fmaf(6.2831853071795865f, u1, -3.1415926535897932f));
+}
+__device__ __forceinline__ double theta_pair(uint2 x, int noise, double) {
+    return theta_of(x, noise, 0.0);
 }
 
 template <class P, int T, bool SAMPLE>
 __global__ void __launch_bounds__(T) k_pair(PairArgs<P> a) {
     using real = typename P::real;
     using vec4 = typename P::vec4;
+    constexpr int NW = T / 32;
+    constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(32) unsigned char smem[];
     const int cap = a.cap;
     const int X = a.X;
     vec4 *s_pos = reinterpret_cast<vec4 *>(smem);
     vec4 *s_vt = s_pos + cap;
     int *s_cs = reinterpret_cast<int *>(s_vt + cap);
-    int *s_pc = s_cs + 9 * (X + 3);                         // pieces: src, dst, len
-    size_t off = (size_t)((unsigned char *)(s_pc + 81) - smem);
-    off = (off + 15) & ~(size_t)15;
+    int *s_pc = s_cs + PAIR_NR * (X + 3);
+    int *s_hr = s_pc + PAIR_NR * 3 * PAIR_PC;        // home rows: staged row, first, count, global
+    size_t off = PairSmem<P>::align16((size_t)((unsigned char *)(s_hr + 16) - smem));
     real *s_a = reinterpret_cast<real *>(smem + off);
-    uint16_t *s_hit = reinterpret_cast<uint16_t *>(s_a + PAIR_MAXT * PAIR_MAXT);
+    real *s_rsh = s_a + PAIR_MAXT * PAIR_MAXT;       // per staged row: y, z frame shift
+    off = PairSmem<P>::align16((size_t)((unsigned char *)(s_rsh + 2 * PAIR_NR) - smem));
+    vec4 *s_hp = reinterpret_cast<vec4 *>(smem + off);
+    vec4 *s_hv = s_hp + NW * 32;
+    vec4 *s_acc = s_hv + NW * 32;
+    real *s_acce = reinterpret_cast<real *>(s_acc + NW * 32);
+    uint32_t *s_q = reinterpret_cast<uint32_t *>(s_acce + NW * 32);
 
-    const int tid = threadIdx.x;
-    const int seg = blockIdx.x;
-    const int row = seg / a.segs_per_row;
-    const int x0 = (seg - row * a.segs_per_row) * X;
-    const int cy = row % a.ny, cz = row / a.ny;
-    const int Xe = min(X, a.nx - x0);
-    const int W = Xe + 3;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    int bid = blockIdx.x;
+    const int bx = bid % a.nbx;
+    bid /= a.nbx;
+    const int byi = bid % a.nby, bzi = bid / a.nby;
+    const int x0 = bx * X, y0 = byi * a.BY, z0 = bzi * a.BZ;
+    const int Xe = min(X, a.nx - x0), BYe = min(a.BY, a.ny - y0), BZe = min(a.BZ, a.nz - z0);
+    const int W = Xe + 3;                 // staged cells per row (ux = -1..Xe) + row end
+    const int SY = BYe + 2, NRe = SY * (BZe + 2);
+    const real hx = a.h[0], hy = a.h[1], hz = a.h[2];
 
     for (int e = tid; e < a.ntypes * a.ntypes; e += T) s_a[e] = a.a[e];
     // per staged cell: counts (k = 0..Xe+1 <-> ux = -1..Xe), k = Xe+2 is the row end
-    for (int e = tid; e < 9 * W; e += T) {
-        const int r = e / W, k = e - r * W;
-        int cnt = 0;
-        if (k <= Xe + 1) {
-            const int yy = (cy + (r % 3) - 1 + a.ny) % a.ny;
-            const int zz = (cz + (r / 3) - 1 + a.nz) % a.nz;
-            const int xx = (x0 + k - 1 + a.nx) % a.nx;
-            const uint32_t key = ((uint32_t)zz * a.ny + yy) * a.nx + xx;
-            cnt = (int)(a.cell_start[key + 1] - a.cell_start[key]);
+    for (int r = wid; r < NRe; r += NW) {
+        const int uy = r % SY - 1, uz = r / SY - 1;
+        int yy = y0 + uy, zz = z0 + uz;
+        yy += yy < 0 ? a.ny : (yy >= a.ny ? -a.ny : 0);
+        zz += zz < 0 ? a.nz : (zz >= a.nz ? -a.nz : 0);
+        const uint32_t rowkey = ((uint32_t)zz * a.ny + yy) * a.nx;
+        for (int k = lane; k < W; k += 32) {
+            int cnt = 0;
+            if (k <= Xe + 1) {
+                int xx = x0 + k - 1;
+                xx += xx < 0 ? a.nx : (xx >= a.nx ? -a.nx : 0);
+                cnt = (int)(a.cell_start[rowkey + xx + 1] - a.cell_start[rowkey + xx]);
+            }
+            s_cs[r * W + k] = cnt;
         }
-        s_cs[e] = cnt;
+        if (lane == 0) {
+            real sy, sz;
+            if (P::kOffsets) {       // offset -> brick frame
+                sy = (real)uy * hy;
+                sz = (real)uz * hz;
+            } else {                 // absolute -> brick frame, undoing the row's wrap
+                sy = (real)(uy - yy) * hy;
+                sz = (real)(uz - zz) * hz;
+            }
+            s_rsh[2 * r] = sy;
+            s_rsh[2 * r + 1] = sz;
+        }
     }
     __syncthreads();
-    if (tid < 32) {   // exclusive scan of the 9*W counts: staged start of each cell
+    if (tid < 32) {   // exclusive scan of the counts: staged start of each cell
         int carry = 0;
-        for (int b = 0; b < 9 * W; b += 32) {
-            const int v = (b + tid < 9 * W) ? s_cs[b + tid] : 0;
+        const int tot = NRe * W;
+        for (int b = 0; b < tot; b += 32) {
+            const int v = (b + tid < tot) ? s_cs[b + tid] : 0;
             int inc = v;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const int u = __shfl_up_sync(0xffffffffu, inc, o);
+                const int u = __shfl_up_sync(FULL, inc, o);
                 if (tid >= o) inc += u;
             }
-            if (b + tid < 9 * W) s_cs[b + tid] = carry + inc - v;
-            carry += __shfl_sync(0xffffffffu, inc, 31);
+            if (b + tid < tot) s_cs[b + tid] = carry + inc - v;
+            carry += __shfl_sync(FULL, inc, 31);
         }
     }
     __syncthreads();
-    if (tid < 9) {    // contiguous source runs of each staged row (split at x wraps)
+    if (tid < NRe) {   // contiguous source runs of each staged row (split at x wraps)
         const int r = tid;
-        const int yy = (cy + (r % 3) - 1 + a.ny) % a.ny;
-        const int zz = (cz + (r / 3) - 1 + a.nz) % a.nz;
+        const int uy = r % SY - 1, uz = r / SY - 1;
+        int yy = y0 + uy, zz = z0 + uz;
+        yy += yy < 0 ? a.ny : (yy >= a.ny ? -a.ny : 0);
+        zz += zz < 0 ? a.nz : (zz >= a.nz ? -a.nz : 0);
         const uint32_t rowkey = ((uint32_t)zz * a.ny + yy) * a.nx;
         int np = 0, kfirst = 0;
         for (int k = 1; k <= Xe + 2; ++k) {
-            const bool end = (k == Xe + 2) || ((x0 + k - 1 + a.nx) % a.nx == 0);
-            if (end) {
-                const int xx = (x0 + kfirst - 1 + a.nx) % a.nx;
-                s_pc[r * 9 + np * 3 + 0] = (int)a.cell_start[rowkey + xx];
-                s_pc[r * 9 + np * 3 + 1] = s_cs[r * W + kfirst];
-                s_pc[r * 9 + np * 3 + 2] = s_cs[r * W + k] - s_cs[r * W + kfirst];
+            int xk = x0 + k - 1;
+            xk += xk >= a.nx ? -a.nx : 0;
+            if (k == Xe + 2 || xk == 0) {
+                int xx = x0 + kfirst - 1;
+                xx += xx < 0 ? a.nx : (xx >= a.nx ? -a.nx : 0);
+                int *pc = s_pc + (r * 3 + np) * PAIR_PC;
+                pc[0] = (int)a.cell_start[rowkey + xx];            // first source slot
+                pc[1] = s_cs[r * W + kfirst];                      // first staged slot
+                pc[2] = s_cs[r * W + k] - s_cs[r * W + kfirst];    // length
+                pc[3] = (int)(rowkey + xx);                        // key of its first cell
+                pc[4] = kfirst - 1;                                // ux of its first cell
+                pc[5] = xx;                                        // cx of its first cell
                 ++np;
                 kfirst = k;
             }
         }
-        for (; np < 3; ++np) s_pc[r * 9 + np * 3 + 2] = 0;
+        for (; np < 3; ++np) s_pc[(r * 3 + np) * PAIR_PC + 2] = 0;
+    }
+    if (tid < 4) {     // home rows (ry, rz) = (tid % 2, tid / 2)
+        const int ry = tid % 2, rz = tid / 2;
+        int hcount = 0, first = 0, gfirst = 0, sr = 0;
+        if (ry < BYe && rz < BZe) {
+            sr = (ry + 1) + SY * (rz + 1);
+            const uint32_t rowkey = ((uint32_t)(z0 + rz) * a.ny + (y0 + ry)) * a.nx;
+            gfirst = (int)a.cell_start[rowkey + x0];
+            hcount = (int)(a.cell_start[rowkey + x0 + Xe] - a.cell_start[rowkey + x0]);
+        }
+        s_hr[4 * tid] = sr;
+        s_hr[4 * tid + 1] = first;
+        s_hr[4 * tid + 2] = hcount;
+        s_hr[4 * tid + 3] = gfirst;
+    }
+    __syncthreads();
+    if (tid == 0) {    // home rows' positions in the concatenated home list
+        int run = 0;
+        for (int h = 0; h < 4; ++h) {
+            s_hr[4 * h + 1] = run;
+            run += s_hr[4 * h + 2];
+        }
     }
     __syncthreads();
 
-    const int S = s_cs[9 * W - 1];                       // staged beads in total
-    const int hb_lo = s_cs[4 * W + 1], hb_hi = s_cs[4 * W + Xe + 1];
-    const int H = hb_hi - hb_lo;
-    const int gbase = (int)a.cell_start[((uint32_t)cz * a.ny + cy) * a.nx + x0];
+    const int S = s_cs[NRe * W - 1];
+    const int H = s_hr[13] + s_hr[14];
     const long long sctr = *a.counter;
     const uint32_t s_lo = (uint32_t)(unsigned long long)sctr;
     const uint32_t s_hi = (uint32_t)((unsigned long long)sctr >> 32);
     const int nt = a.ntypes;
-    const int hmax = a.hmax;
+    vec4 *my_hp = s_hp + wid * 32, *my_hv = s_hv + wid * 32, *my_acc = s_acc + wid * 32;
+    real *my_acce = s_acce + wid * 32;
+    uint32_t *my_q = s_q + wid * PAIR_HMAX * 32;
+    const unsigned lt_mask = (1u << lane) - 1u;
     int staged_lo = -1;
 
     for (int hb0 = 0; hb0 < H; hb0 += T) {
         const int hb = hb0 + tid;
         const bool active = hb < H;
-        const int g = gbase + (active ? hb : 0);
-        vec4 pi = a.pos[g], vi = a.vt[g];
-        int cxi = 0, cyi = cy, czi = cz, uxi = 0;
+        // which home row, global slot, frame coordinates
+        int hr = 0;
+        if (active)
+            while (hr < 3 && hb >= s_hr[4 * (hr + 1) + 1]) ++hr;
+        const int g = active ? s_hr[4 * hr + 3] + (hb - s_hr[4 * hr + 1]) : 0;
+        const int ry = hr % 2, rz = hr / 2;
+        const int sr_home = s_hr[4 * hr];
+        const vec4 pr = a.pos[g];
+        int uxi = 0;
+        vec4 hp = pr;
         if (active) {
-            cxi = (int)(a.key[g] % (uint32_t)a.nx);
-            uxi = cxi - x0;
+            const uint32_t rowkey = ((uint32_t)(z0 + rz) * a.ny + (y0 + ry)) * a.nx;
+            uxi = (int)(a.key[g] - rowkey) - x0;
+            if (P::kOffsets) {
+                hp.x = (real)uxi * hx + pr.x;
+                hp.y = (real)ry * hy + pr.y;
+                hp.z = (real)rz * hz + pr.z;
+            } else {
+                hp.x = pr.x - (real)x0 * hx;
+                hp.y = pr.y - (real)y0 * hy;
+                hp.z = pr.z - (real)z0 * hz;
+            }
         }
-        const int ti = (int)pi.w;
-        const int32_t idi = P::unpack_id(vi.w);
-        real fx = 0, fy = 0, fz = 0, wc = 0, ep = 0;
+        my_hp[lane] = hp;
+        my_hv[lane] = a.vt[g];
+        my_acc[lane] = mk4<vec4, real>((real)0, (real)0, (real)0, (real)0);
+        my_acce[lane] = (real)0;
+        // distances from the bead to the faces of its cell (pruning)
+        const real lxd = hp.x - (real)uxi * hx, uxd = hx - lxd;
+        const real lyd = hp.y - (real)ry * hy, uyd = hy - lyd;
+        const real lzd = hp.z - (real)rz * hz, uzd = hz - lzd;
+        const real cut2 = (real)1.0001;
 
         for (int c0 = 0; c0 < S; c0 += cap) {
             const int c1 = min(S, c0 + cap);
             if (staged_lo != c0) {
                 __syncthreads();   // everyone is done with the previous chunk
-                const int wid = tid >> 5, lane = tid & 31;
-                for (int pc = wid; pc < 27; pc += T / 32) {
-                    const int src = s_pc[pc * 3], dst = s_pc[pc * 3 + 1], len = s_pc[pc * 3 + 2];
+                for (int pcn = wid; pcn < NRe * 3; pcn += NW) {
+                    const int *pc = s_pc + pcn * PAIR_PC;
+                    const int src = pc[0], dst = pc[1], len = pc[2];
                     const int lo = max(dst, c0), hi = min(dst + len, c1);
+                    if (lo >= hi) continue;
+                    const int r = pcn / 3;
+                    const uint32_t k0 = (uint32_t)pc[3];
+                    const int ux0 = pc[4];
+                    const real shx = (real)(ux0 - pc[5]) * hx;
+                    const real sy = s_rsh[2 * r], sz = s_rsh[2 * r + 1];
                     for (int q = lo + lane; q < hi; q += 32) {
-                        s_pos[q - c0] = a.pos[src + (q - dst)];
-                        s_vt[q - c0] = a.vt[src + (q - dst)];
+                        const int gq = src + (q - dst);
+                        vec4 p = a.pos[gq];
+                        if (P::kOffsets) p.x = (real)((int)(a.key[gq] - k0) + ux0) * hx + p.x;
+                        else p.x = p.x + shx;
+                        p.y += sy;
+                        p.z += sz;
+                        s_pos[q - c0] = p;
+                        s_vt[q - c0] = a.vt[gq];
                     }
                 }
                 staged_lo = c0;
                 __syncthreads();
             }
-            if (!active) continue;
-            int ci = 0, q = 0;
-            bool more = true;
-            while (more) {
-                // scan: collect up to hmax hits in (cell, slot) order
+            __syncwarp();
+            const real xi = hp.x, yi = hp.y, zi = hp.z;
+            int r9 = 0, q = 0;
+            bool more = active;
+            while (__any_sync(FULL, more)) {
+                // ---- scan: up to PAIR_HMAX hits, rows (dz, dy) ascending, slots ascending
                 int nh = 0;
-                more = false;
-                for (; ci < 27; ++ci) {
-                    const int rr = ci / 3;
-                    const int k = uxi + (ci - 3 * rr);
-                    const int qb = max(s_cs[rr * W + k], c0);
-                    const int qe = min(s_cs[rr * W + k + 1], c1);
-                    if (q < qb) q = qb;
-                    if (q >= qe) continue;
-                    real sx, sy, sz;
-                    cell_shift<P>(a, ci, cxi, cyi, czi, sx, sy, sz);
-                    const real bx = pi.x + sx, by = pi.y + sy, bz = pi.z + sz;
-                    for (; q < qe; ++q) {
-                        const vec4 pj = s_pos[q - c0];
-                        const real dx = bx - pj.x, dy = by - pj.y, dz = bz - pj.z;
-                        const real r2 = dx * dx + dy * dy + dz * dz;
-                        if (r2 < (real)1 && r2 > (real)0) {
-                            s_hit[nh * T + tid] = (uint16_t)(((q - c0) << 5) | ci);
-                            if (++nh == hmax) break;
+                if (more) {
+                    for (; r9 < 9; ++r9) {
+                        const int dy = r9 % 3 - 1, dz = r9 / 3 - 1;
+                        const real ey = dy < 0 ? lyd : (dy > 0 ? uyd : (real)0);
+                        const real ez = dz < 0 ? lzd : (dz > 0 ? uzd : (real)0);
+                        const real dyz = ey * ey + ez * ez;
+                        if (dyz >= cut2) continue;                       // row out of reach
+                        const int sr = sr_home + dy + SY * dz;
+                        const int* cs = s_cs + sr * W + uxi;
+                        const int qb = max(dyz + lxd * lxd < cut2 ? cs[0] : cs[1], c0);
+                        const int qe_full = min(dyz + uxd * uxd < cut2 ? cs[3] : cs[2], c1);
+                        if (q < qb) q = qb;
+                        if (q >= qe_full) continue;
+                        int qe = qe_full;
+                        if (qe - q > PAIR_HMAX - nh) {
+                            if (nh > 0) break;                   // evaluate first, resume here
+                            qe = q + PAIR_HMAX;                  // a crowded row: part of it
+                        }
+                        for (; q < qe; ++q) {
+                            const vec4 pj = s_pos[q - c0];
+                            const real dx = xi - pj.x, dyv = yi - pj.y, dzv = zi - pj.z;
+                            const real r2 = dx * dx + dyv * dyv + dzv * dzv;
+                            if (r2 < (real)1 && r2 > (real)0) {
+                                my_q[nh * 32 + lane] = (uint32_t)(q - c0) | ((uint32_t)nh << 11) |
+                                                       ((uint32_t)lane << 15);
+                                ++nh;
+                            }
+                        }
+                        if (q < qe_full) break;
+                    }
+                    more = r9 < 9;
+                }
+                __syncwarp();
+                // ---- compact level by level: all first hits, then all second hits, ...
+                int K = 0;
+                for (int m = 0; m < PAIR_HMAX; ++m) {
+                    const unsigned A = __ballot_sync(FULL, nh > m);
+                    if (A == 0u) break;
+                    if (A != FULL || K != 32 * m) {
+                        uint32_t e = 0;
+                        if (nh > m) e = my_q[m * 32 + lane];
+                        __syncwarp();
+                        if (nh > m) my_q[K + __popc(A & lt_mask)] = e;
+                        __syncwarp();
+                    }
+                    K += __popc(A);
+                }
+                // ---- evaluate 32 hits at a time, sums updated level by level
+                for (int b = 0; b < K; b += 32) {
+                    const int f = b + lane;
+                    const bool valid = f < K;
+                    const uint32_t e = valid ? my_q[f] : 0u;
+                    const int jl = (int)(e & 2047u), lvl = (int)((e >> 11) & 15u);
+                    const int owner = (int)(e >> 15);
+                    real fx = 0, fy = 0, fz = 0, wc = 0, ep = 0;
+                    if (valid) {
+                        const vec4 hpo = my_hp[owner], hvo = my_hv[owner];
+                        const vec4 pj = s_pos[jl], vj = s_vt[jl];
+                        const real dx = hpo.x - pj.x, dyv = hpo.y - pj.y, dzv = hpo.z - pj.z;
+                        const real r2 = dx * dx + dyv * dyv + dzv * dzv;
+                        const real rinv = rsqrt_r(r2);
+                        const real rr1 = r2 * rinv;
+                        const real w = (real)1 - rr1;
+                        const real ex = dx * rinv, ey = dyv * rinv, ez = dzv * rinv;
+                        const real evel = ex * (hvo.x - vj.x) + ey * (hvo.y - vj.y) + ez * (hvo.z - vj.z);
+                        const real aij = s_a[(int)hpo.w * nt + (int)pj.w];
+                        const int32_t idi = P::unpack_id(hvo.w), idj = P::unpack_id(vj.w);
+                        const uint32_t lo = (uint32_t)min(idi, idj), hi = (uint32_t)max(idi, idj);
+                        const uint2 rnd = philox_rk(lo, hi, s_lo, s_hi, a.rk);
+                        const real th = theta_pair(rnd, a.noise, (real)0);
+                        const real fc = aij * w;
+                        const real mag = fc - a.gamma * w * w * evel + a.sig_sqdt * w * th;
+                        fx = mag * ex;
+                        fy = mag * ey;
+                        fz = mag * ez;
+                        if (SAMPLE) {
+                            wc = rr1 * fc;
+                            ep = (real)0.5 * fc * w;
                         }
                     }
-                    if (nh == hmax) {
-                        ++q;
-                        more = true;
-                        break;
+                    const int lv_lo = __shfl_sync(FULL, lvl, 0);
+                    const int lv_hi = __shfl_sync(FULL, lvl, min(31, K - 1 - b));
+                    for (int lv = lv_lo; lv <= lv_hi; ++lv) {
+                        if (valid && lvl == lv) {
+                            vec4 s = my_acc[owner];
+                            s.x += fx;
+                            s.y += fy;
+                            s.z += fz;
+                            if (SAMPLE) {
+                                s.w += wc;
+                                my_acce[owner] += ep;
+                            }
+                            my_acc[owner] = s;
+                        }
+                        __syncwarp();
                     }
                 }
-                // evaluate the hits in order
-                for (int m = 0; m < nh; ++m) {
-                    const int e = s_hit[m * T + tid];
-                    const int jl = e >> 5, cj = e & 31;
-                    real sx, sy, sz;
-                    cell_shift<P>(a, cj, cxi, cyi, czi, sx, sy, sz);
-                    const vec4 pj = s_pos[jl], vj = s_vt[jl];
-                    const real dx = pi.x + sx - pj.x, dy = pi.y + sy - pj.y, dz = pi.z + sz - pj.z;
-                    const real r2 = dx * dx + dy * dy + dz * dz;
-                    const real rinv = rsqrt_r(r2);
-                    const real r = r2 * rinv;
-                    const real w = (real)1 - r;
-                    const real ex = dx * rinv, ey = dy * rinv, ez = dz * rinv;
-                    const real evel = ex * (vi.x - vj.x) + ey * (vi.y - vj.y) + ez * (vi.z - vj.z);
-                    const int tj = (int)pj.w;
-                    const real aij = s_a[ti * nt + tj];
-                    const int32_t idj = P::unpack_id(vj.w);
-                    const uint32_t lo = (uint32_t)min(idi, idj), hi = (uint32_t)max(idi, idj);
-                    const uint2 rnd = philox_xy(lo, hi, s_lo, s_hi, a.key0, a.key1);
-                    const real th = theta_of(rnd, a.noise, (real)0);
-                    const real fc = aij * w;
-                    const real mag = fc - a.gamma * w * w * evel + a.sig_sqdt * w * th;
-                    fx += mag * ex;
-                    fy += mag * ey;
-                    fz += mag * ez;
-                    if (SAMPLE) {
-                        wc += r * fc;
-                        ep += (real)0.5 * fc * w;
-                    }
-                }
+                __syncwarp();
             }
         }
         if (active) {
-            a.fpair[g] = mk4<vec4, real>(fx, fy, fz, (real)0);
-            if (SAMPLE) a.ev[g] = mk4<vec4, real>(wc, ep, (real)0, (real)0);
+            const vec4 s = my_acc[lane];
+            a.fpair[g] = mk4<vec4, real>(s.x, s.y, s.z, (real)0);
+            if (SAMPLE) a.ev[g] = mk4<vec4, real>(s.w, my_acce[lane], (real)0, (real)0);
         }
+        __syncwarp();
     }
 }
 
@@ -838,9 +1043,9 @@ __global__ void __launch_bounds__(256) k_unpermute(int n, Geo g, const typename 
     if (P::kOffsets) {
         int cx, cy, cz;
         decode_key(key[t], g, cx, cy, cz);
-        x = wrap_exact((double)cx * g.h[0] + x, g.L[0]);
-        y = wrap_exact((double)cy * g.h[1] + y, g.L[1]);
-        z = wrap_exact((double)cz * g.h[2] + z, g.L[2]);
+        x = wrap_fast((double)cx * g.h[0] + x, g.L[0]);
+        y = wrap_fast((double)cy * g.h[1] + y, g.L[1]);
+        z = wrap_fast((double)cz * g.h[2] + z, g.L[2]);
     }
     opos[3 * i] = x; opos[3 * i + 1] = y; opos[3 * i + 2] = z;
     ovel[3 * i] = v.x; ovel[3 * i + 1] = v.y; ovel[3 * i + 2] = v.z;
