@@ -210,6 +210,62 @@ int dpd_cells_noalloc(const double *pos_dev, int64_t n, const dpd_box *box, uint
 /* Free the handle and its device memory (NULL is allowed). */
 int dpd_destroy(dpd_handle *h);
 
+/* ---- batches: many independent systems advanced by the same launches ----
+ * A batch owns fixed pools sized at creation.  Systems are added (with their
+ * state) and removed at any time between steps; dpd_batch_step advances
+ * every resident system by the same number of steps, each with its own box,
+ * parameters, seed and step counter, in one launch per kernel of Fig. 1's
+ * loop for all of them (CUDA-graph replayed).  A system draws the same noise
+ * and follows the same arithmetic alone or in a batch: per-bead sums are in
+ * a fixed order and ids, cell keys and Philox counters are its own.
+ * Memory admission: dpd_batch_add fails with DPD_ENOMEM when the system's
+ * beads, cells (floor(L) per dimension, multiplied), pair-kernel bricks or
+ * bond records (two per bond) do not fit next to the resident systems; the
+ * caller keeps it queued and retries after a removal. */
+typedef struct dpd_batch dpd_batch;
+
+typedef struct {
+    int64_t max_beads;     /* bead pool                                      */
+    int64_t max_cells;     /* cell pool (also bounds the pair-kernel bricks) */
+    int64_t max_bonds;     /* bond pool, in bonds (each uses two records)    */
+    int32_t max_systems;   /* resident systems at once                       */
+    int32_t pad;
+} dpd_batch_capacity;
+
+/* Create an empty batch.  opt: precision, threads, use_graph, cuda_stream
+ * (and noise as the default for added systems); NULL = defaults. */
+int dpd_batch_create(const dpd_batch_capacity *cap, const dpd_options *opt, dpd_batch **out);
+
+/* Add a system with its parameters (as dpd_create) and its state (as
+ * dpd_set_state); *sys receives its index.  lambda and seed are per system.
+ * Synchronises.  Errors: DPD_EINVAL, DPD_ENOMEM (does not fit: not admitted),
+ * DPD_ECUDA. */
+int dpd_batch_add(dpd_batch *b, const dpd_box *box, int64_t n, const int32_t *types,
+                  int32_t ntypes, const double *a_ij, double gamma, double kT, double dt,
+                  const dpd_bond *bonds, int64_t nbonds, const dpd_bond *morse, int64_t nmorse,
+                  double lambda, uint64_t seed, const double *pos, const double *vel,
+                  int64_t step, int32_t *sys);
+
+/* Remove system sys and re-pack the others.  Synchronises. */
+int dpd_batch_remove(dpd_batch *b, int32_t sys);
+
+/* Advance every resident system by nsteps (asynchronous). */
+int dpd_batch_step(dpd_batch *b, int64_t nsteps);
+
+/* State and observables of one system (as dpd_get_state / dpd_observables). */
+int dpd_batch_get_state(dpd_batch *b, int32_t sys, double *pos, double *vel, double *force,
+                        int64_t *step);
+int dpd_batch_observables(dpd_batch *b, int32_t sys, dpd_obs *out);
+
+/* Pool use: used[4] and cap[4] = beads, cells, bricks, bond records;
+ * *nsys = resident systems.  Any pointer may be NULL. */
+int dpd_batch_usage(const dpd_batch *b, int64_t used[4], int64_t cap[4], int32_t *nsys);
+
+int dpd_batch_sync(dpd_batch *b);
+int64_t dpd_batch_launch_count(const dpd_batch *b);
+const char *dpd_batch_last_error(const dpd_batch *b);
+int dpd_batch_destroy(dpd_batch *b);
+
 /* Static string for a DPD_E* code. */
 const char *dpd_strerror(int code);
 

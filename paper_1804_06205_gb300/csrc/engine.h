@@ -10,7 +10,7 @@
 
 namespace dpd {
 
-// Everything dpd_create validated, in the layout the engines upload.
+// One system, as dpd_create / dpd_batch_add validated it.
 struct Config {
     double L[3];
     int64_t n;
@@ -20,10 +20,7 @@ struct Config {
     double gamma, kT, dt, lambda;
     uint64_t seed;
     int32_t noise;
-    int32_t sample_every;
-    int32_t tile_cells, threads;
-    bool use_graph;
-    void *stream;                    // cudaStream_t or nullptr
+    int32_t tile_cells;              // brick length override (0 = automatic)
     // bonded records in CSR by bead id: both ends hold the record
     std::vector<int32_t> bptr;       // [n+1]
     std::vector<int32_t> bpartner;   // [2*nbonds]
@@ -35,27 +32,44 @@ struct Config {
     double h[3], inv_h[3];
 };
 
-class EngineBase {
+// The pools of a batch and the engine-wide options.
+struct BatchConfig {
+    int64_t max_beads, max_cells, max_bonds;   // bond records count both ends
+    int32_t max_systems;
+    int32_t threads;                 // pair-kernel threads per block (0 = auto)
+    int32_t sample_every;            // running means every k steps (0 = off)
+    bool use_graph;
+    void *stream;                    // cudaStream_t or nullptr
+};
+
+class BatchBase {
   public:
-    virtual ~EngineBase() {}
-    virtual int set_state(const double *pos, const double *vel, int64_t step) = 0;
+    virtual ~BatchBase() {}
+    // Reserve space for a system and its parameters; *slot names it.
+    virtual int add_system(const Config &cfg, int *slot) = 0;
+    virtual int remove_system(int slot) = 0;
+    virtual int set_state(int slot, const double *pos, const double *vel, int64_t step) = 0;
+    // Advance every resident system (all must have a state).
     virtual int step(int64_t nsteps) = 0;
-    virtual int get_state(double *pos, double *vel, double *force, int64_t *step) = 0;
-    virtual int observables(dpd_obs *out) = 0;
-    virtual int gr(double rmax, int32_t nbins, uint64_t *counts) = 0;
-    virtual int get_cells(uint32_t *key_by_id, int64_t *order, int64_t *cell_start) = 0;
+    virtual int get_state(int slot, double *pos, double *vel, double *force, int64_t *step) = 0;
+    virtual int observables(int slot, dpd_obs *out) = 0;
+    virtual int gr(int slot, double rmax, int32_t nbins, uint64_t *counts) = 0;
+    virtual int get_cells(int slot, uint32_t *key_by_id, int64_t *order, int64_t *cell_start) = 0;
     virtual int sync() = 0;
     virtual int64_t launches() const = 0;
     virtual int profile_begin(int64_t max_steps) = 0;
     virtual int profile_end(double ms[3], int64_t *nsteps) = 0;
+    // used[4] / cap[4]: beads, cells, bricks, bond records
+    virtual void usage(int64_t used[4], int64_t cap[4]) const = 0;
+    virtual int nlive() const = 0;
     const char *last_error() const { return err_.c_str(); }
 
   protected:
     std::string err_;
 };
 
-// Returns nullptr and sets *rc on failure.
-EngineBase *make_engine_f32(const Config &cfg, int *rc, std::string *err);
-EngineBase *make_engine_f64(const Config &cfg, int *rc, std::string *err);
+// Returns nullptr and sets *rc / *err on failure.
+BatchBase *make_batch_f32(const BatchConfig &bc, int *rc, std::string *err);
+BatchBase *make_batch_f64(const BatchConfig &bc, int *rc, std::string *err);
 
 }  // namespace dpd

@@ -1,11 +1,11 @@
-// FP32 engine: FP32 pair and bond forces, positions stored as FP32 offsets
-// inside their cell, FP64 for the wrap, the cell keys and the reductions.
+// FP32 batch engine: FP32 pair and bond forces, positions stored as FP32 offsets
+// inside their cell; FP64 for the initial wrap, the cell keys and the reductions.
 #include "engine_impl.cuh"
 
 namespace dpd {
 
-EngineBase *make_engine_f32(const Config &cfg, int *rc, std::string *err) {
-    Engine<PF32> *e = new Engine<PF32>(cfg);
+BatchBase *make_batch_f32(const BatchConfig &bc, int *rc, std::string *err) {
+    BatchEngine<PF32> *e = new BatchEngine<PF32>(bc);
     *rc = e->init();
     if (*rc) {
         *err = e->last_error();

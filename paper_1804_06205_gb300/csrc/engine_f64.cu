@@ -1,11 +1,11 @@
-// FP64 engine: the plain FP64 path, absolute FP64 positions and FP64
+// FP64 batch engine: the plain FP64 path, absolute FP64 positions and FP64
 // arithmetic in every kernel.
 #include "engine_impl.cuh"
 
 namespace dpd {
 
-EngineBase *make_engine_f64(const Config &cfg, int *rc, std::string *err) {
-    Engine<PF64> *e = new Engine<PF64>(cfg);
+BatchBase *make_batch_f64(const BatchConfig &bc, int *rc, std::string *err) {
+    BatchEngine<PF64> *e = new BatchEngine<PF64>(bc);
     *rc = e->init();
     if (*rc) {
         *err = e->last_error();

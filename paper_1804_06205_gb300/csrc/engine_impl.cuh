@@ -1,8 +1,15 @@
-// Per-precision engine: owns the device state of one DPD system and
-// sequences the kernels of kernels.cuh (Fig. 1 of arxiv 1804.06205).
+// Per-precision batch engine: owns the device pools of any number of
+// resident DPD systems and sequences the kernels of kernels.cuh (Fig. 1 of
+// arxiv 1804.06205) over all of them.  A single system is a batch of one.
+//
+// Pools.  Systems are packed one after another, in the same order, in every
+// pool: beads [bead0, bead0+n), cells [cell0, cell0+ncell), pair-kernel
+// bricks [brick0, ...), bond records [bond0, ...).  Adding a system appends
+// it; removing one re-packs the survivors (k_relayout) between steps.
 #pragma once
 
 #include <algorithm>
+#include <cmath>
 #include <memory>
 
 #include "kernels.cuh"
@@ -18,10 +25,25 @@ namespace dpd {
         }                                                                         \
     } while (0)
 
+static __global__ void k_fill_int(int *p, int n, int v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
 template <class P>
-class Engine : public EngineBase {
+class BatchEngine : public BatchBase {
     using real = typename P::real;
     using vec4 = typename P::vec4;
+
+    struct SysHost {
+        Config cfg;
+        bool live = false, has_state = false;
+        int n = 0, ncell = 0, nbrick = 0, nbond = 0;
+        int bead0 = 0, cell0 = 0, brick0 = 0, bond0 = 0;
+        int X = 1, BY = 1, BZ = 1, nbx = 1, nby = 1, nbz = 1, cap = 64;
+        int64_t step = 0;
+        int red0 = 0, nred = 0, rsys_index = 0;   // reduction chunks, entry in rsys
+    };
 
     struct GraphSlot {
         cudaGraph_t graph = nullptr;
@@ -32,190 +54,284 @@ class Engine : public EngineBase {
     };
 
   public:
-    explicit Engine(const Config &c) : cfg_(c) {}
+    explicit BatchEngine(const BatchConfig &bc) : bc_(bc) {}
 
-    ~Engine() override {
+    ~BatchEngine() override {
         if (stream_) cudaStreamSynchronize(stream_);
-        for (auto &row : graphs_)
-            for (auto &g : row) {
-                if (g.exec) cudaGraphExecDestroy(g.exec);
-                if (g.graph) cudaGraphDestroy(g.graph);
-            }
+        drop_graphs();
         for (cudaEvent_t e : prof_ev_) cudaEventDestroy(e);
         for (cudaEvent_t e : ph_)
             if (e) cudaEventDestroy(e);
         for (void *p : allocs_) cudaFree(p);
-        if (io_host_) cudaFreeHost(io_host_);
         if (own_stream_ && stream_) cudaStreamDestroy(stream_);
     }
 
     int init() {
-        n_ = (int)cfg_.n;
-        geo_.nx = cfg_.nc[0];
-        geo_.ny = cfg_.nc[1];
-        geo_.nz = cfg_.nc[2];
-        geo_.ncell = geo_.nx * geo_.ny * geo_.nz;
-        for (int k = 0; k < 3; ++k) {
-            geo_.L[k] = cfg_.L[k];
-            geo_.h[k] = cfg_.h[k];
-            geo_.inv_h[k] = cfg_.inv_h[k];
-        }
-        if (cfg_.stream) {
-            stream_ = (cudaStream_t)cfg_.stream;
+        NB_ = (int)bc_.max_beads;
+        NC_ = (int)bc_.max_cells;
+        NBR_ = NC_;                      // a brick holds at least one cell
+        NBD_ = (int)std::max<int64_t>(bc_.max_bonds, 1);
+        NS_ = std::max(1, bc_.max_systems);
+        NRB_ = NB_ / RED_CHUNK + NS_ + 1;
+        T_ = bc_.threads > 0 ? bc_.threads : 128;
+        if (T_ != 64 && T_ != 128 && T_ != 256) T_ = 128;
+        if (bc_.stream) {
+            stream_ = (cudaStream_t)bc_.stream;
         } else {
             DPD_CU(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking));
             own_stream_ = true;
         }
-        const size_t N = (size_t)n_, C = (size_t)geo_.ncell;
+        const size_t N = (size_t)NB_, C = (size_t)NC_;
         int rc;
         if ((rc = alloc(&pos_, N)) || (rc = alloc(&pos_tmp_, N)) || (rc = alloc(&vel_[0], N)) ||
             (rc = alloc(&vel_[1], N)) || (rc = alloc(&frc_[0], N)) || (rc = alloc(&frc_[1], N)) ||
             (rc = alloc(&vt_, N)) || (rc = alloc(&fpair_, N)) || (rc = alloc(&ev_, N)) ||
             (rc = alloc(&key_, N)) || (rc = alloc(&key_tmp_, N)) || (rc = alloc(&rank_, N)) ||
             (rc = alloc(&src_, N)) || (rc = alloc(&sid_, N)) || (rc = alloc(&id_[0], N)) ||
-            (rc = alloc(&id_[1], N)) || (rc = alloc(&inv_perm_, N)) ||
+            (rc = alloc(&id_[1], N)) || (rc = alloc(&inv_perm_, N)) || (rc = alloc(&bsys_, N)) ||
             (rc = alloc(&count_, C)) || (rc = alloc(&cell_start_, C + 1)) ||
-            (rc = alloc(&bsum_, C / SCAN_B + 2)) || (rc = alloc(&counter_, 1)) ||
-            (rc = alloc(&status_, 1)) || (rc = alloc(&partial_, RED_BLOCKS * RED_K)) ||
-            (rc = alloc(&obs_, RED_K)) || (rc = alloc(&acc_, 4)) ||
-            (rc = alloc(&io_, 9 * N)) || (rc = alloc(&types_, N)) ||
-            (rc = alloc(&a_, (size_t)cfg_.ntypes * cfg_.ntypes)) ||
-            (rc = alloc(&bptr_, N + 1)) || (rc = alloc(&bpartner_, cfg_.bpartner.size() + 1)) ||
-            (rc = alloc(&bpar_, cfg_.bpartner.size() + 1)))
+            (rc = alloc(&bsum_, C / SCAN_B + 2)) || (rc = alloc(&brick_sys_, (size_t)NBR_)) ||
+            (rc = alloc(&sys_, (size_t)NS_)) || (rc = alloc(&counter_, (size_t)NS_)) ||
+            (rc = alloc(&status_, 1)) || (rc = alloc(&atab_, (size_t)NS_ * PAIR_MAXT * PAIR_MAXT)) ||
+            (rc = alloc(&bptr_, N + 1)) || (rc = alloc(&bpartner_, (size_t)NBD_)) ||
+            (rc = alloc(&bpar_, (size_t)NBD_)) || (rc = alloc(&rmap_, (size_t)NRB_)) ||
+            (rc = alloc(&rsys_, (size_t)NS_)) || (rc = alloc(&partial_, (size_t)NRB_ * RED_K)) ||
+            (rc = alloc(&obs_, (size_t)NS_ * RED_K)) || (rc = alloc(&acc_, (size_t)NS_ * 4)) ||
+            (rc = alloc(&old_bead0_, (size_t)NS_)))
             return rc;
         for (auto &e : ph_) DPD_CU(cudaEventCreate(&e));
         DPD_CU(cudaMemsetAsync(count_, 0, C * sizeof(uint32_t), stream_));
         DPD_CU(cudaMemsetAsync(status_, 0, sizeof(int), stream_));
-        DPD_CU(cudaMemsetAsync(acc_, 0, 4 * sizeof(double), stream_));
+        DPD_CU(cudaMemsetAsync(acc_, 0, (size_t)NS_ * 4 * sizeof(double), stream_));
+        DPD_CU(cudaMemsetAsync(obs_, 0, (size_t)NS_ * RED_K * sizeof(double), stream_));
         DPD_CU(cudaMemsetAsync(ev_, 0, N * sizeof(vec4), stream_));
-        DPD_CU(cudaMemcpyAsync(types_, cfg_.types.data(), N * sizeof(int32_t),
-                               cudaMemcpyHostToDevice, stream_));
-        std::vector<real> a(cfg_.a.begin(), cfg_.a.end());
-        DPD_CU(cudaMemcpyAsync(a_, a.data(), a.size() * sizeof(real), cudaMemcpyHostToDevice,
-                               stream_));
-        DPD_CU(cudaMemcpyAsync(bptr_, cfg_.bptr.data(), (N + 1) * sizeof(int32_t),
-                               cudaMemcpyHostToDevice, stream_));
-        const size_t nb = cfg_.bpartner.size();
-        if (nb) {
-            std::vector<vec4> bp(nb);
-            for (size_t b = 0; b < nb; ++b) {
-                bp[b].x = (real)cfg_.br0[b];
-                bp[b].y = (real)cfg_.bk[b];
-                bp[b].z = (real)cfg_.balpha[b];
-                bp[b].w = (real)cfg_.bkind[b];
+        DPD_CU(cudaMemsetAsync(bptr_, 0, (N + 1) * sizeof(int32_t), stream_));
+        DPD_CU(cudaStreamSynchronize(stream_));
+        hs_.resize(NS_);
+        hsys_.resize(NS_);
+        return DPD_OK;
+    }
+
+    // ------------------------------------------------------------ membership
+    int add_system(const Config &c, int *slot) override {
+        int s = -1;
+        for (int k = 0; k < NS_; ++k)
+            if (!hs_[k].live) {
+                s = k;
+                break;
             }
-            DPD_CU(cudaMemcpyAsync(bpartner_, cfg_.bpartner.data(), nb * sizeof(int32_t),
+        if (s < 0) {
+            err_ = "no free system slot";
+            return DPD_ENOMEM;
+        }
+        SysHost h;
+        h.cfg = c;
+        h.n = (int)c.n;
+        h.ncell = c.nc[0] * c.nc[1] * c.nc[2];
+        h.nbond = (int)c.bpartner.size();
+        choose_tiles(h);
+        if (used_beads_ + h.n > NB_ || used_cells_ + h.ncell > NC_ ||
+            used_bricks_ + h.nbrick > NBR_ || used_bonds_ + h.nbond > NBD_) {
+            err_ = "the system does not fit in the batch's pools";
+            return DPD_ENOMEM;
+        }
+        h.bead0 = used_beads_;
+        h.cell0 = used_cells_;
+        h.brick0 = used_bricks_;
+        h.bond0 = used_bonds_;
+        h.live = true;
+        hs_[s] = std::move(h);
+        order_.push_back(s);
+        int rc = upload_system(s);
+        if (rc) {
+            hs_[s].live = false;
+            order_.pop_back();
+            return rc;
+        }
+        used_beads_ += hs_[s].n;
+        used_cells_ += hs_[s].ncell;
+        used_bricks_ += hs_[s].nbrick;
+        used_bonds_ += hs_[s].nbond;
+        if ((rc = rebuild_reduce_maps()) || (rc = update_smem())) return rc;
+        drop_graphs();
+        *slot = s;
+        return DPD_OK;
+    }
+
+    int remove_system(int s) override {
+        if (s < 0 || s >= NS_ || !hs_[s].live) return DPD_EINVAL;
+        int rc = check_status();
+        if (rc) return rc;
+        std::vector<int> old0(NS_, 0);
+        for (int k : order_) old0[k] = hs_[k].bead0;
+        hs_[s].live = false;
+        order_.erase(std::find(order_.begin(), order_.end(), s));
+        // re-pack the survivors in order
+        used_beads_ = used_cells_ = used_bricks_ = used_bonds_ = 0;
+        for (int k : order_) {
+            SysHost &h = hs_[k];
+            h.bead0 = used_beads_;
+            h.cell0 = used_cells_;
+            h.brick0 = used_bricks_;
+            h.bond0 = used_bonds_;
+            used_beads_ += h.n;
+            used_cells_ += h.ncell;
+            used_bricks_ += h.nbrick;
+            used_bonds_ += h.nbond;
+            if ((rc = upload_system(k))) return rc;
+        }
+        if ((rc = rebuild_reduce_maps()) || (rc = update_smem())) return rc;
+        if (used_beads_ > 0) {
+            DPD_CU(cudaMemcpyAsync(old_bead0_, old0.data(), NS_ * sizeof(int),
                                    cudaMemcpyHostToDevice, stream_));
-            DPD_CU(cudaMemcpyAsync(bpar_, bp.data(), nb * sizeof(vec4), cudaMemcpyHostToDevice,
-                                   stream_));
+            RelayoutArgs<P> ra;
+            ra.n_new = used_beads_;
+            ra.bsys_new = bsys_;
+            ra.sys_new = sys_;
+            ra.old_bead0 = old_bead0_;
+            ra.pos = pos_;
+            ra.vel = vel_[cur_];
+            ra.frc = frc_[cur_];
+            ra.key = key_;
+            ra.id = id_[cur_];
+            ra.pos_out = pos_tmp_;
+            ra.vel_out = vel_[cur_ ^ 1];
+            ra.frc_out = frc_[cur_ ^ 1];
+            ra.key_out = key_tmp_;
+            ra.id_out = id_[cur_ ^ 1];
+            k_relayout<P><<<blocks(used_beads_), 256, 0, stream_>>>(ra);
+            ++launches_;
+            DPD_CU(cudaGetLastError());
+            std::swap(pos_, pos_tmp_);
+            std::swap(key_, key_tmp_);
+            cur_ ^= 1;
         }
         DPD_CU(cudaStreamSynchronize(stream_));
-        choose_tiles();
-        return set_pair_smem();
+        drop_graphs();
+        return DPD_OK;
     }
 
     // ---------------------------------------------------------------- state
-    int set_state(const double *pos, const double *vel, int64_t step) override {
+    int set_state(int s, const double *pos, const double *vel, int64_t step) override {
+        if (s < 0 || s >= NS_ || !hs_[s].live) return DPD_EINVAL;
         int rc = check_status();
         if (rc) return rc;
-        const size_t N = (size_t)n_;
-        DPD_CU(cudaMemcpyAsync(io_, pos, 3 * N * sizeof(double), cudaMemcpyHostToDevice, stream_));
-        DPD_CU(cudaMemcpyAsync(io_ + 3 * N, vel, 3 * N * sizeof(double), cudaMemcpyHostToDevice,
+        SysHost &h = hs_[s];
+        const size_t n = (size_t)h.n;
+        if ((rc = ensure_io(n))) return rc;
+        DPD_CU(cudaMemcpyAsync(io_, pos, 3 * n * sizeof(double), cudaMemcpyHostToDevice, stream_));
+        DPD_CU(cudaMemcpyAsync(io_ + 3 * n, vel, 3 * n * sizeof(double), cudaMemcpyHostToDevice,
                                stream_));
+        int32_t *types_d = reinterpret_cast<int32_t *>(io_ + 6 * n);
+        DPD_CU(cudaMemcpyAsync(types_d, h.cfg.types.data(), n * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, stream_));
+        // the initial binning writes the "old" buffers; the sort brings the
+        // system into the current ones, leaving the other systems untouched
+        const int old = cur_ ^ 1;
         InitArgs<P> ia;
-        ia.n = n_;
-        ia.g = geo_;
+        ia.s = s;
+        ia.sys = sys_;
         ia.pos_in = io_;
-        ia.vel_in = io_ + 3 * N;
-        ia.types = types_;
+        ia.vel_in = io_ + 3 * n;
+        ia.types = types_d;
         ia.pos_tmp = pos_tmp_;
-        ia.vel = vel_[cur_];      // "old" order = bead-id order
-        ia.frc = frc_[cur_];
+        ia.vel = vel_[old];
+        ia.frc = frc_[old];
         ia.key_tmp = key_tmp_;
         ia.rank = rank_;
         ia.count = count_;
-        ia.id = id_[cur_];
+        ia.id = id_[old];
         ia.status = status_;
-        k_init<P><<<blocks(n_), 256, 0, stream_>>>(ia);
+        k_init<P><<<blocks(h.n), 256, 0, stream_>>>(ia);
         ++launches_;
         DPD_CU(cudaGetLastError());
-        host_step_ = step;
-        long long s = (long long)step;
-        DPD_CU(cudaMemcpyAsync(counter_, &s, sizeof(long long), cudaMemcpyHostToDevice, stream_));
-        rc = enqueue_sort();
-        if (rc) return rc;
-        if ((rc = launch_pair(true)) || (rc = enqueue_bonds(true, true, false))) return rc;
+        long long sv = (long long)step;
+        DPD_CU(cudaMemcpyAsync(counter_ + s, &sv, sizeof(long long), cudaMemcpyHostToDevice,
+                               stream_));
+        if ((rc = enqueue_sort(h.bead0, h.bead0 + h.n, h.cell0, h.cell0 + h.ncell, old, cur_)) ||
+            (rc = launch_pair(true, h.brick0, h.nbrick)) ||
+            (rc = enqueue_bonds(true, true, h.bead0, h.bead0 + h.n)) ||
+            (rc = enqueue_reduce(h.red0, h.nred, h.rsys_index, 1, false)))
+            return rc;
         DPD_CU(cudaStreamSynchronize(stream_));
         int st = 0;
         DPD_CU(cudaMemcpy(&st, status_, sizeof(int), cudaMemcpyDeviceToHost));
         if (st & ST_BADINPUT) {
             st &= ~ST_BADINPUT;
             DPD_CU(cudaMemcpy(status_, &st, sizeof(int), cudaMemcpyHostToDevice));
-            has_state_ = false;
+            h.has_state = false;
             err_ = "non-finite position or velocity";
             return DPD_EINVAL;
         }
-        has_state_ = true;
+        h.has_state = true;
+        h.step = step;
         return check_status();
     }
 
     int step(int64_t nsteps) override {
-        if (!has_state_) return DPD_ENOSTATE;
         if (nsteps < 0) return DPD_EINVAL;
+        if (order_.empty()) return nsteps == 0 ? DPD_OK : DPD_ENOSTATE;
+        for (int k : order_)
+            if (!hs_[k].has_state) return DPD_ENOSTATE;
         int rc = peek_status();
         if (rc) return rc;
         for (int64_t k = 0; k < nsteps; ++k) {
-            const int64_t s = host_step_ + 1;
-            const bool acc = cfg_.sample_every > 0 && (s % cfg_.sample_every) == 0;
+            // running means: one system's steps decide when (a batch of one)
+            const bool acc = bc_.sample_every > 0 && order_.size() == 1 &&
+                             ((hs_[order_[0]].step + 1) % bc_.sample_every) == 0;
             const bool sample = acc || (k == nsteps - 1);
             const int variant = acc ? 2 : (sample ? 1 : 0);
-            if (cfg_.use_graph) {
-                rc = launch_graph(variant);
-            } else {
-                rc = enqueue_step(sample, acc);
-            }
+            rc = bc_.use_graph ? launch_graph(variant) : enqueue_step(sample, acc, false);
             if (rc) return rc;
-            host_step_ = s;
+            for (int s : order_) hs_[s].step += 1;
         }
         return DPD_OK;
     }
 
-    int get_state(double *pos, double *vel, double *force, int64_t *step) override {
-        if (!has_state_) return DPD_ENOSTATE;
-        const size_t N = (size_t)n_;
-        k_unpermute<P><<<blocks(n_), 256, 0, stream_>>>(n_, geo_, pos_, key_, vel_[cur_],
-                                                        frc_[cur_], id_[cur_], io_, io_ + 3 * N,
-                                                        io_ + 6 * N);
+    int get_state(int s, double *pos, double *vel, double *force, int64_t *step) override {
+        if (s < 0 || s >= NS_ || !hs_[s].live) return DPD_EINVAL;
+        SysHost &h = hs_[s];
+        if (!h.has_state) return DPD_ENOSTATE;
+        const size_t n = (size_t)h.n;
+        int rc = ensure_io(n);
+        if (rc) return rc;
+        k_unpermute<P><<<blocks(h.n), 256, 0, stream_>>>(s, sys_, pos_, key_, vel_[cur_],
+                                                         frc_[cur_], id_[cur_], io_, io_ + 3 * n,
+                                                         io_ + 6 * n);
         ++launches_;
         DPD_CU(cudaGetLastError());
         if (pos)
-            DPD_CU(cudaMemcpyAsync(pos, io_, 3 * N * sizeof(double), cudaMemcpyDeviceToHost,
+            DPD_CU(cudaMemcpyAsync(pos, io_, 3 * n * sizeof(double), cudaMemcpyDeviceToHost,
                                    stream_));
         if (vel)
-            DPD_CU(cudaMemcpyAsync(vel, io_ + 3 * N, 3 * N * sizeof(double),
+            DPD_CU(cudaMemcpyAsync(vel, io_ + 3 * n, 3 * n * sizeof(double),
                                    cudaMemcpyDeviceToHost, stream_));
         if (force)
-            DPD_CU(cudaMemcpyAsync(force, io_ + 6 * N, 3 * N * sizeof(double),
+            DPD_CU(cudaMemcpyAsync(force, io_ + 6 * n, 3 * n * sizeof(double),
                                    cudaMemcpyDeviceToHost, stream_));
         DPD_CU(cudaStreamSynchronize(stream_));
-        if (step) *step = host_step_;
+        if (step) *step = h.step;
         return check_status();
     }
 
-    int observables(dpd_obs *out) override {
-        if (!has_state_) return DPD_ENOSTATE;
+    int observables(int s, dpd_obs *out) override {
+        if (s < 0 || s >= NS_ || !hs_[s].live) return DPD_EINVAL;
+        SysHost &h = hs_[s];
+        if (!h.has_state) return DPD_ENOSTATE;
         double o[RED_K], acc[4];
-        DPD_CU(cudaMemcpyAsync(o, obs_, sizeof(o), cudaMemcpyDeviceToHost, stream_));
-        DPD_CU(cudaMemcpyAsync(acc, acc_, sizeof(acc), cudaMemcpyDeviceToHost, stream_));
+        DPD_CU(cudaMemcpyAsync(o, obs_ + (size_t)s * RED_K, sizeof(o), cudaMemcpyDeviceToHost,
+                               stream_));
+        DPD_CU(cudaMemcpyAsync(acc, acc_ + (size_t)s * 4, sizeof(acc), cudaMemcpyDeviceToHost,
+                               stream_));
         DPD_CU(cudaStreamSynchronize(stream_));
         std::memset(out, 0, sizeof(*out));
-        const double V = geo_.L[0] * geo_.L[1] * geo_.L[2];
-        out->step = host_step_;
+        const double V = h.cfg.L[0] * h.cfg.L[1] * h.cfg.L[2];
+        out->step = h.step;
         out->momentum[0] = o[0];
         out->momentum[1] = o[1];
         out->momentum[2] = o[2];
         out->sum_v2 = o[3];
-        out->kT = n_ > 1 ? o[3] / (3.0 * n_ - 3.0) : 0.0;
+        out->kT = h.n > 1 ? o[3] / (3.0 * h.n - 3.0) : 0.0;
         out->p_ideal = o[3] / (3.0 * V);
         out->p_cons = o[4] / (3.0 * V);
         out->p_bond = o[6] / (3.0 * V);
@@ -229,14 +345,15 @@ class Engine : public EngineBase {
         return out->status;
     }
 
-    int gr(double rmax, int32_t nbins, uint64_t *counts) override {
-        if (!has_state_) return DPD_ENOSTATE;
+    int gr(int s, double rmax, int32_t nbins, uint64_t *counts) override {
+        if (s < 0 || s >= NS_ || !hs_[s].live) return DPD_EINVAL;
+        SysHost &h = hs_[s];
+        if (!h.has_state) return DPD_ENOSTATE;
         if (!(rmax > 0) || nbins <= 0 || nbins > 4096 || !counts) return DPD_EINVAL;
         int K[3];
         for (int k = 0; k < 3; ++k) {
-            K[k] = (int)std::ceil(rmax * geo_.inv_h[k]);
-            const int nck = k == 0 ? geo_.nx : (k == 1 ? geo_.ny : geo_.nz);
-            if (2 * K[k] + 1 > nck) {
+            K[k] = (int)std::ceil(rmax * h.cfg.inv_h[k]);
+            if (2 * K[k] + 1 > h.cfg.nc[k]) {
                 err_ = "dpd_gr: rmax too large for the cell grid";
                 return DPD_EINVAL;
             }
@@ -245,8 +362,8 @@ class Engine : public EngineBase {
         DPD_CU(cudaMallocAsync((void **)&d, nbins * sizeof(unsigned long long), stream_));
         DPD_CU(cudaMemsetAsync(d, 0, nbins * sizeof(unsigned long long), stream_));
         const double dr = rmax / (double)nbins;
-        k_gr<P><<<blocks(n_), 256, nbins * sizeof(unsigned long long), stream_>>>(
-            n_, geo_, K[0], K[1], K[2], pos_, key_, cell_start_, rmax, dr, nbins, d);
+        k_gr<P><<<blocks(h.n), 256, nbins * sizeof(unsigned long long), stream_>>>(
+            s, sys_, K[0], K[1], K[2], pos_, key_, cell_start_, rmax, dr, nbins, d);
         ++launches_;
         DPD_CU(cudaGetLastError());
         DPD_CU(cudaMemcpyAsync(counts, d, nbins * sizeof(unsigned long long),
@@ -256,29 +373,33 @@ class Engine : public EngineBase {
         return check_status();
     }
 
-    int get_cells(uint32_t *key_by_id, int64_t *order, int64_t *cell_start) override {
-        if (!has_state_) return DPD_ENOSTATE;
-        const size_t N = (size_t)n_, C = (size_t)geo_.ncell;
+    int get_cells(int s, uint32_t *key_by_id, int64_t *order, int64_t *cell_start) override {
+        if (s < 0 || s >= NS_ || !hs_[s].live) return DPD_EINVAL;
+        SysHost &h = hs_[s];
+        if (!h.has_state) return DPD_ENOSTATE;
+        const size_t n = (size_t)h.n, C = (size_t)h.ncell;
+        int rc = ensure_io(n);
+        if (rc) return rc;
         uint32_t *dk = reinterpret_cast<uint32_t *>(io_);
-        int64_t *dord = reinterpret_cast<int64_t *>(io_ + 3 * N);
-        k_cells_out<<<blocks(n_), 256, 0, stream_>>>(n_, key_, id_[cur_], dk, dord);
+        int64_t *dord = reinterpret_cast<int64_t *>(io_ + 3 * n);
+        k_cells_out<P><<<blocks(h.n), 256, 0, stream_>>>(s, sys_, key_, id_[cur_], dk, dord);
         ++launches_;
         DPD_CU(cudaGetLastError());
         if (key_by_id)
-            DPD_CU(cudaMemcpyAsync(key_by_id, dk, N * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+            DPD_CU(cudaMemcpyAsync(key_by_id, dk, n * sizeof(uint32_t), cudaMemcpyDeviceToHost,
                                    stream_));
         if (order)
-            DPD_CU(cudaMemcpyAsync(order, dord, N * sizeof(int64_t), cudaMemcpyDeviceToHost,
+            DPD_CU(cudaMemcpyAsync(order, dord, n * sizeof(int64_t), cudaMemcpyDeviceToHost,
                                    stream_));
         std::vector<uint32_t> cs;
         if (cell_start) {
             cs.resize(C + 1);
-            DPD_CU(cudaMemcpyAsync(cs.data(), cell_start_, (C + 1) * sizeof(uint32_t),
+            DPD_CU(cudaMemcpyAsync(cs.data(), cell_start_ + h.cell0, (C + 1) * sizeof(uint32_t),
                                    cudaMemcpyDeviceToHost, stream_));
         }
         DPD_CU(cudaStreamSynchronize(stream_));
         if (cell_start)
-            for (size_t c = 0; c <= C; ++c) cell_start[c] = cs[c];
+            for (size_t c = 0; c <= C; ++c) cell_start[c] = (int64_t)cs[c] - h.bead0;
         return check_status();
     }
 
@@ -314,6 +435,19 @@ class Engine : public EngineBase {
         return profile_release();
     }
 
+    void usage(int64_t used[4], int64_t cap[4]) const override {
+        used[0] = used_beads_;
+        used[1] = used_cells_;
+        used[2] = used_bricks_;
+        used[3] = used_bonds_;
+        cap[0] = NB_;
+        cap[1] = NC_;
+        cap[2] = NBR_;
+        cap[3] = NBD_;
+    }
+
+    int nlive() const override { return (int)order_.size(); }
+
   private:
     // ---------------------------------------------------------------- helpers
     template <class T>
@@ -329,7 +463,366 @@ class Engine : public EngineBase {
         return DPD_OK;
     }
 
+    // staging for one system's host <-> device copies (9 doubles per bead)
+    int ensure_io(size_t n) {
+        if (io_n_ >= n) return DPD_OK;
+        double *q = nullptr;
+        const int rc = alloc(&q, 9 * n);
+        if (rc) return rc;
+        io_ = q;
+        io_n_ = n;
+        return DPD_OK;
+    }
+
     static int blocks(int n, int t = 256) { return std::max(1, (n + t - 1) / t); }
+
+    int peek_status() { return status_host_; }
+
+    int check_status() {
+        if (!status_) return DPD_OK;
+        int st = 0;
+        cudaError_t e = cudaMemcpy(&st, status_, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            err_ = std::string("status read: ") + cudaGetErrorString(e);
+            return DPD_ECUDA;
+        }
+        if (st & ST_TIMEOUT) status_host_ = DPD_ETIMEOUT;
+        else if (st & ST_NONFINITE) status_host_ = DPD_EUNSTABLE;
+        if (status_host_ == DPD_EUNSTABLE) err_ = "non-finite position, velocity or observable";
+        return status_host_;
+    }
+
+    // Brick shape of one system: X x 2 x 2 cells holding about 0.85 T beads,
+    // with the length near that which wastes the fewest cells along x.
+    void choose_tiles(SysHost &h) const {
+        const Config &c = h.cfg;
+        h.BY = std::min(2, c.nc[1]);
+        h.BZ = std::min(2, c.nc[2]);
+        const double per_cell = (double)h.n / (double)h.ncell;
+        int xmax = c.tile_cells > 0
+                       ? c.tile_cells
+                       : (int)std::floor(0.85 * T_ / (h.BY * h.BZ * std::max(per_cell, 0.25)));
+        xmax = std::max(1, std::min(xmax, PAIR_MAXX));
+        int X = xmax;
+        if (c.tile_cells <= 0) {
+            int best = xmax, waste = 1 << 30;
+            for (int x = std::max(1, xmax - 2); x <= std::min(PAIR_MAXX, xmax + 1); ++x) {
+                const int w = ((c.nc[0] + x - 1) / x) * x - c.nc[0];
+                if (w < waste) {
+                    waste = w;
+                    best = x;
+                }
+            }
+            X = best;
+        }
+        h.X = std::min(X, c.nc[0]);
+        h.nbx = (c.nc[0] + h.X - 1) / h.X;
+        h.nby = (c.nc[1] + h.BY - 1) / h.BY;
+        h.nbz = (c.nc[2] + h.BZ - 1) / h.BZ;
+        h.nbrick = h.nbx * h.nby * h.nbz;
+        // staged capacity: the mean of (BY+2)(BZ+2)(X+2) cells plus ~4 sigma;
+        // larger neighbourhoods are staged in chunks (slots must fit 11 bits)
+        const double mean = (h.BY + 2) * (h.BZ + 2) * (h.X + 2) * per_cell;
+        int cap = (int)std::ceil(mean + 4.0 * std::sqrt(mean) + 32.0);
+        cap = (cap + 31) / 32 * 32;
+        const int cap_max = (int)((96 * 1024) / (2 * sizeof(vec4)));
+        h.cap = std::max(64, std::min(cap, std::min(cap_max, 2016)));
+    }
+
+    // Descriptor, bead -> system and brick -> system maps, a_ij table and
+    // bond records of system s at its current place in the pools.
+    int upload_system(int s) {
+        SysHost &h = hs_[s];
+        const Config &c = h.cfg;
+        SysDesc<P> &d = hsys_[s];
+        std::memset(&d, 0, sizeof(d));
+        d.n = h.n;
+        d.bead0 = h.bead0;
+        d.cell0 = h.cell0;
+        d.ncell = h.ncell;
+        d.nx = c.nc[0];
+        d.ny = c.nc[1];
+        d.nz = c.nc[2];
+        d.ntypes = c.ntypes;
+        d.brick0 = h.brick0;
+        d.X = h.X;
+        d.BY = h.BY;
+        d.BZ = h.BZ;
+        d.nbx = h.nbx;
+        d.nby = h.nby;
+        d.nbz = h.nbz;
+        d.cap = h.cap;
+        d.a_off = s * PAIR_MAXT * PAIR_MAXT;
+        d.noise = c.noise;
+        for (int k = 0; k < 3; ++k) {
+            d.L[k] = c.L[k];
+            d.h[k] = c.h[k];
+            d.inv_h[k] = c.inv_h[k];
+            d.hf[k] = (float)c.h[k];
+            d.inv_hf[k] = (float)c.inv_h[k];
+        }
+        d.dt = (real)c.dt;
+        d.half_dt2 = (real)(0.5 * c.dt * c.dt);
+        d.half_dt = (real)(0.5 * c.dt);
+        d.lam_dt = (real)(c.lambda * c.dt);
+        d.gamma = (real)c.gamma;
+        d.sig_sqdt = (real)(std::sqrt(2.0 * c.gamma * c.kT) / std::sqrt(c.dt));
+        {   // Philox round keys: (k0, k1) + r (0x9E3779B9, 0xBB67AE85)
+            uint32_t k0 = (uint32_t)(c.seed & 0xffffffffull), k1 = (uint32_t)(c.seed >> 32);
+            for (int r = 0; r < 10; ++r) {
+                d.rk[2 * r] = k0;
+                d.rk[2 * r + 1] = k1;
+                k0 += 0x9E3779B9u;
+                k1 += 0xBB67AE85u;
+            }
+        }
+        DPD_CU(cudaMemcpyAsync(sys_ + s, &d, sizeof(d), cudaMemcpyHostToDevice, stream_));
+        k_fill_int<<<blocks(h.n), 256, 0, stream_>>>(bsys_ + h.bead0, h.n, s);
+        k_fill_int<<<blocks(h.nbrick), 256, 0, stream_>>>(brick_sys_ + h.brick0, h.nbrick, s);
+        launches_ += 2;
+        DPD_CU(cudaGetLastError());
+        std::vector<real> a(c.a.begin(), c.a.end());
+        DPD_CU(cudaMemcpyAsync(atab_ + d.a_off, a.data(), a.size() * sizeof(real),
+                               cudaMemcpyHostToDevice, stream_));
+        std::vector<int32_t> bp(c.bptr.begin(), c.bptr.end());
+        for (auto &v : bp) v += h.bond0;
+        DPD_CU(cudaMemcpyAsync(bptr_ + h.bead0, bp.data(), bp.size() * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, stream_));
+        const size_t nb = c.bpartner.size();
+        std::vector<vec4> par(nb);
+        if (nb) {
+            for (size_t b = 0; b < nb; ++b) {
+                par[b].x = (real)c.br0[b];
+                par[b].y = (real)c.bk[b];
+                par[b].z = (real)c.balpha[b];
+                par[b].w = (real)c.bkind[b];
+            }
+            DPD_CU(cudaMemcpyAsync(bpartner_ + h.bond0, c.bpartner.data(), nb * sizeof(int32_t),
+                                   cudaMemcpyHostToDevice, stream_));
+            DPD_CU(cudaMemcpyAsync(bpar_ + h.bond0, par.data(), nb * sizeof(vec4),
+                                   cudaMemcpyHostToDevice, stream_));
+        }
+        // the host vectors above must outlive the asynchronous copies
+        DPD_CU(cudaStreamSynchronize(stream_));
+        return DPD_OK;
+    }
+
+    // Reduction chunks of every live system, in pool order.
+    int rebuild_reduce_maps() {
+        std::vector<int2> rmap;
+        std::vector<int4> rsys;
+        for (int s : order_) {
+            SysHost &h = hs_[s];
+            h.red0 = (int)rmap.size();
+            for (int b = 0; b < h.n; b += RED_CHUNK)
+                rmap.push_back(make_int2(h.bead0 + b, h.bead0 + std::min(h.n, b + RED_CHUNK)));
+            h.nred = (int)rmap.size() - h.red0;
+            h.rsys_index = (int)rsys.size();
+            rsys.push_back(make_int4(s, h.red0, h.nred, 0));
+        }
+        nred_all_ = (int)rmap.size();
+        nrsys_all_ = (int)rsys.size();
+        if (nred_all_ > NRB_) {
+            err_ = "too many reduction chunks";
+            return DPD_ENOMEM;
+        }
+        if (!rmap.empty())
+            DPD_CU(cudaMemcpyAsync(rmap_, rmap.data(), rmap.size() * sizeof(int2),
+                                   cudaMemcpyHostToDevice, stream_));
+        if (!rsys.empty())
+            DPD_CU(cudaMemcpyAsync(rsys_, rsys.data(), rsys.size() * sizeof(int4),
+                                   cudaMemcpyHostToDevice, stream_));
+        DPD_CU(cudaStreamSynchronize(stream_));
+        return DPD_OK;
+    }
+
+    // shared memory of the pair kernel: the largest brick among live systems
+    int update_smem() {
+        int capmax = 64, xmax = 1;
+        for (int s : order_) {
+            capmax = std::max(capmax, hs_[s].cap);
+            xmax = std::max(xmax, hs_[s].X);
+        }
+        if (capmax != capmax_ || xmax != xmax_) drop_graphs();
+        capmax_ = capmax;
+        xmax_ = xmax;
+        smem_ = PairSmem<P>::bytes(capmax_, xmax_, T_);
+        int rc;
+        switch (T_) {
+            case 64:
+                if ((rc = set_pair_smem_t<64, true>())) return rc;
+                return set_pair_smem_t<64, false>();
+            case 256:
+                if ((rc = set_pair_smem_t<256, true>())) return rc;
+                return set_pair_smem_t<256, false>();
+            default:
+                if ((rc = set_pair_smem_t<128, true>())) return rc;
+                return set_pair_smem_t<128, false>();
+        }
+    }
+
+    // (the attribute is per kernel, shared by all handles: only ever raised)
+    template <int T, bool S>
+    int set_pair_smem_t() {
+        if (smem_ <= 48 * 1024) return DPD_OK;
+        cudaFuncAttributes fa;
+        DPD_CU(cudaFuncGetAttributes(&fa, k_pair<P, T, S>));
+        if ((size_t)fa.maxDynamicSharedSizeBytes >= smem_) return DPD_OK;
+        DPD_CU(cudaFuncSetAttribute(k_pair<P, T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem_));
+        return DPD_OK;
+    }
+
+    template <int T, bool S>
+    int launch_pair_t(const PairLaunch<P> &pl, int nbr) {
+        k_pair<P, T, S><<<nbr, T, smem_, stream_>>>(pl);
+        ++launches_;
+        DPD_CU(cudaGetLastError());
+        return DPD_OK;
+    }
+
+    int launch_pair(bool sample, int br_lo, int nbr) {
+        if (nbr <= 0) return DPD_OK;
+        PairLaunch<P> pl;
+        pl.sys = sys_;
+        pl.brick_sys = brick_sys_;
+        pl.br_lo = br_lo;
+        pl.capmax = capmax_;
+        pl.Xmax = xmax_;
+        pl.pos = pos_;
+        pl.vt = vt_;
+        pl.key = key_;
+        pl.cell_start = cell_start_;
+        pl.fpair = fpair_;
+        pl.ev = ev_;
+        pl.atab = atab_;
+        pl.counter = counter_;
+        switch (T_) {
+            case 64:
+                return sample ? launch_pair_t<64, true>(pl, nbr) : launch_pair_t<64, false>(pl, nbr);
+            case 256:
+                return sample ? launch_pair_t<256, true>(pl, nbr) : launch_pair_t<256, false>(pl, nbr);
+            default:
+                return sample ? launch_pair_t<128, true>(pl, nbr) : launch_pair_t<128, false>(pl, nbr);
+        }
+    }
+
+    // cell division of beads [b_lo, b_hi) / cells [c_lo, c_hi), from the
+    // `old` velocity/force/id buffers into the `nxt` ones
+    int enqueue_sort(int b_lo, int b_hi, int c_lo, int c_hi, int old, int nxt) {
+        const int C = c_hi - c_lo, nb = (C + SCAN_B - 1) / SCAN_B;
+        k_scan1<<<nb, SCAN_T, 0, stream_>>>(count_ + c_lo, C, bsum_);
+        k_scan2b<<<1, SCAN_T, 0, stream_>>>(bsum_, nb, cell_start_ + c_lo, C, (uint32_t)b_lo);
+        k_scan3<<<nb, SCAN_T, 0, stream_>>>(count_ + c_lo, C, bsum_, cell_start_ + c_lo);
+        ScatterArgs<P> sa;
+        sa.b_lo = b_lo;
+        sa.b_hi = b_hi;
+        sa.sys = sys_;
+        sa.bsys = bsys_;
+        sa.key_tmp = key_tmp_;
+        sa.rank = rank_;
+        sa.cell_start = cell_start_;
+        sa.id_old = id_[old];
+        sa.src = src_;
+        sa.sid = sid_;
+        k_scatter<P><<<blocks(b_hi - b_lo), 256, 0, stream_>>>(sa);
+        k_cellfix<<<blocks(C), 256, 0, stream_>>>(c_lo, c_hi, cell_start_, src_, sid_);
+        GatherArgs<P> ga;
+        ga.b_lo = b_lo;
+        ga.b_hi = b_hi;
+        ga.sys = sys_;
+        ga.bsys = bsys_;
+        ga.src = src_;
+        ga.sid = sid_;
+        ga.pos_tmp = pos_tmp_;
+        ga.vel_old = vel_[old];
+        ga.frc_old = frc_[old];
+        ga.key_tmp = key_tmp_;
+        ga.pos = pos_;
+        ga.vel = vel_[nxt];
+        ga.frc = frc_[nxt];
+        ga.vt = vt_;
+        ga.key = key_;
+        ga.id = id_[nxt];
+        ga.inv_perm = inv_perm_;
+        k_gather<P><<<blocks(b_hi - b_lo), 256, 0, stream_>>>(ga);
+        launches_ += 6;
+        DPD_CU(cudaGetLastError());
+        return DPD_OK;
+    }
+
+    // bonds (+ velocity update unless init) over beads [b_lo, b_hi)
+    int enqueue_bonds(bool init, bool sample, int b_lo, int b_hi) {
+        BondArgs<P> ba;
+        ba.b_lo = b_lo;
+        ba.b_hi = b_hi;
+        ba.sys = sys_;
+        ba.bsys = bsys_;
+        ba.fpair = fpair_;
+        ba.pos = pos_;
+        ba.key = key_;
+        ba.id = id_[cur_];
+        ba.inv_perm = inv_perm_;
+        ba.bptr = bptr_;
+        ba.bpartner = bpartner_;
+        ba.bpar = bpar_;
+        ba.vel = vel_[cur_];
+        ba.frc = frc_[cur_];
+        ba.ev = ev_;
+        const int g = blocks(b_hi - b_lo);
+        if (init) {
+            if (sample) k_bond_vel<P, true, true><<<g, 256, 0, stream_>>>(ba);
+            else k_bond_vel<P, true, false><<<g, 256, 0, stream_>>>(ba);
+        } else {
+            if (sample) k_bond_vel<P, false, true><<<g, 256, 0, stream_>>>(ba);
+            else k_bond_vel<P, false, false><<<g, 256, 0, stream_>>>(ba);
+        }
+        ++launches_;
+        DPD_CU(cudaGetLastError());
+        return DPD_OK;
+    }
+
+    // FP64 observables of systems rsys[k0 .. k0+nk) from chunks [r0, r0+nr)
+    int enqueue_reduce(int r0, int nr, int k0, int nk, bool accumulate) {
+        if (nr <= 0 || nk <= 0) return DPD_OK;
+        k_reduce<P><<<nr, RED_T, 0, stream_>>>(rmap_ + r0, vel_[cur_], ev_, partial_ + r0 * RED_K);
+        k_reduce_final<P><<<nk, 32, 0, stream_>>>(rsys_ + k0, sys_, partial_, obs_, acc_,
+                                                  accumulate ? 1 : 0, status_);
+        launches_ += 2;
+        DPD_CU(cudaGetLastError());
+        return DPD_OK;
+    }
+
+    int enqueue_step(bool sample, bool accumulate, bool capturing) {
+        int rc = mark(0, capturing);
+        if (rc) return rc;
+        UpdArgs<P> ua;
+        ua.b_lo = 0;
+        ua.b_hi = used_beads_;
+        ua.sys = sys_;
+        ua.bsys = bsys_;
+        ua.key = key_;
+        ua.pos = pos_;
+        ua.vel = vel_[cur_];
+        ua.frc = frc_[cur_];
+        ua.pos_tmp = pos_tmp_;
+        ua.key_tmp = key_tmp_;
+        ua.rank = rank_;
+        ua.count = count_;
+        ua.counter = counter_;
+        ua.status = status_;
+        k_update<P><<<blocks(used_beads_), 256, 0, stream_>>>(ua);
+        ++launches_;
+        DPD_CU(cudaGetLastError());
+        const int nxt = cur_ ^ 1;
+        if ((rc = enqueue_sort(0, used_beads_, 0, used_cells_, cur_, nxt))) return rc;
+        cur_ = nxt;
+        if ((rc = mark(1, capturing)) || (rc = launch_pair(sample, 0, used_bricks_)) ||
+            (rc = mark(2, capturing)) || (rc = enqueue_bonds(false, sample, 0, used_beads_)))
+            return rc;
+        if (sample && (rc = enqueue_reduce(0, nred_all_, 0, nrsys_all_, accumulate))) return rc;
+        return mark(3, capturing);
+    }
 
     // Phase boundary k (0..3) of the step being enqueued: a placeholder event
     // while a graph is captured, a timing event when profiling direct launches.
@@ -371,250 +864,18 @@ class Engine : public EngineBase {
         return DPD_OK;
     }
 
-    int peek_status() {
-        if (status_host_) return status_host_;
-        return DPD_OK;
-    }
-
-    int check_status() {
-        if (!status_) return DPD_OK;
-        int st = 0;
-        cudaError_t e = cudaMemcpy(&st, status_, sizeof(int), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) {
-            err_ = std::string("status read: ") + cudaGetErrorString(e);
-            return DPD_ECUDA;
-        }
-        if (st & ST_TIMEOUT) status_host_ = DPD_ETIMEOUT;
-        else if (st & ST_NONFINITE) status_host_ = DPD_EUNSTABLE;
-        if (status_host_ == DPD_EUNSTABLE) err_ = "non-finite position, velocity or observable";
-        return status_host_;
-    }
-
-    void choose_tiles() {
-        // threads per block; bricks of X x 2 x 2 cells holding about 0.85 T beads
-        T_ = cfg_.threads > 0 ? cfg_.threads : 128;
-        if (T_ != 64 && T_ != 128 && T_ != 256) T_ = 128;
-        BY_ = std::min(2, geo_.ny);
-        BZ_ = std::min(2, geo_.nz);
-        const double per_cell = (double)n_ / (double)geo_.ncell;
-        int xmax = cfg_.tile_cells > 0
-                       ? cfg_.tile_cells
-                       : (int)std::floor(0.85 * T_ / (BY_ * BZ_ * std::max(per_cell, 0.25)));
-        xmax = std::max(1, std::min(xmax, PAIR_MAXX));
-        X_ = xmax;
-        if (cfg_.tile_cells <= 0) {   // the length near xmax that wastes the fewest cells
-            int best = xmax, waste = 1 << 30;
-            for (int x = std::max(1, xmax - 2); x <= std::min(PAIR_MAXX, xmax + 1); ++x) {
-                const int w = ((geo_.nx + x - 1) / x) * x - geo_.nx;
-                if (w < waste) {
-                    waste = w;
-                    best = x;
-                }
+    void drop_graphs() {
+        for (auto &row : graphs_)
+            for (auto &g : row) {
+                if (g.exec) cudaGraphExecDestroy(g.exec);
+                if (g.graph) cudaGraphDestroy(g.graph);
+                g = GraphSlot();
             }
-            X_ = best;
-        }
-        X_ = std::min(X_, geo_.nx);
-        nbx_ = (geo_.nx + X_ - 1) / X_;
-        nby_ = (geo_.ny + BY_ - 1) / BY_;
-        nbz_ = (geo_.nz + BZ_ - 1) / BZ_;
-        nseg_ = nbx_ * nby_ * nbz_;
-        // staged capacity: the mean of (BY+2)(BZ+2)(X+2) cells plus ~4 sigma;
-        // larger neighbourhoods are staged in chunks (slots must fit 11 bits)
-        const double mean = (BY_ + 2) * (BZ_ + 2) * (X_ + 2) * per_cell;
-        int cap = (int)std::ceil(mean + 4.0 * std::sqrt(mean) + 32.0);
-        cap = (cap + 31) / 32 * 32;
-        const int cap_max = (int)((96 * 1024) / (2 * sizeof(vec4)));
-        cap_ = std::max(64, std::min(cap, std::min(cap_max, 2016)));
-        smem_ = PairSmem<P>::bytes(cap_, X_, T_);
     }
-
-    // dynamic shared memory above the 48 KB default, set once (not while a
-    // graph is being captured)
-    // (the attribute is per kernel, shared by all handles: only ever raised)
-    template <int T, bool S>
-    int set_pair_smem_t() {
-        if (smem_ <= 48 * 1024) return DPD_OK;
-        cudaFuncAttributes fa;
-        DPD_CU(cudaFuncGetAttributes(&fa, k_pair<P, T, S>));
-        if ((size_t)fa.maxDynamicSharedSizeBytes >= smem_) return DPD_OK;
-        DPD_CU(cudaFuncSetAttribute(k_pair<P, T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem_));
-        return DPD_OK;
-    }
-
-    int set_pair_smem() {
-        int rc;
-        switch (T_) {
-            case 64:
-                if ((rc = set_pair_smem_t<64, true>())) return rc;
-                return set_pair_smem_t<64, false>();
-            case 256:
-                if ((rc = set_pair_smem_t<256, true>())) return rc;
-                return set_pair_smem_t<256, false>();
-            default:
-                if ((rc = set_pair_smem_t<128, true>())) return rc;
-                return set_pair_smem_t<128, false>();
-        }
-    }
-
-    template <int T, bool S>
-    int launch_pair_t(const PairArgs<P> &pa) {
-        k_pair<P, T, S><<<nseg_, T, smem_, stream_>>>(pa);
-        ++launches_;
-        DPD_CU(cudaGetLastError());
-        return DPD_OK;
-    }
-
-    int launch_pair(bool sample) {
-        PairArgs<P> pa;
-        pa.pos = pos_;
-        pa.vt = vt_;
-        pa.key = key_;
-        pa.cell_start = cell_start_;
-        pa.fpair = fpair_;
-        pa.ev = ev_;
-        pa.a = a_;
-        pa.ntypes = cfg_.ntypes;
-        pa.nx = geo_.nx;
-        pa.ny = geo_.ny;
-        pa.nz = geo_.nz;
-        pa.X = X_;
-        pa.BY = BY_;
-        pa.BZ = BZ_;
-        pa.nbx = nbx_;
-        pa.nby = nby_;
-        for (int k = 0; k < 3; ++k) pa.h[k] = (real)geo_.h[k];
-        pa.gamma = (real)cfg_.gamma;
-        pa.sig_sqdt = (real)(std::sqrt(2.0 * cfg_.gamma * cfg_.kT) / std::sqrt(cfg_.dt));
-        {   // Philox round keys: (k0, k1) + r (0x9E3779B9, 0xBB67AE85)
-            uint32_t k0 = (uint32_t)(cfg_.seed & 0xffffffffull), k1 = (uint32_t)(cfg_.seed >> 32);
-            for (int r = 0; r < 10; ++r) {
-                pa.rk[2 * r] = k0;
-                pa.rk[2 * r + 1] = k1;
-                k0 += 0x9E3779B9u;
-                k1 += 0xBB67AE85u;
-            }
-        }
-        pa.noise = cfg_.noise;
-        pa.counter = counter_;
-        pa.cap = cap_;
-        switch (T_) {
-            case 64: return sample ? launch_pair_t<64, true>(pa) : launch_pair_t<64, false>(pa);
-            case 256: return sample ? launch_pair_t<256, true>(pa) : launch_pair_t<256, false>(pa);
-            default: return sample ? launch_pair_t<128, true>(pa) : launch_pair_t<128, false>(pa);
-        }
-    }
-
-    int enqueue_sort() {
-        const int C = geo_.ncell;
-        const int nb = (C + SCAN_B - 1) / SCAN_B;
-        k_scan1<<<nb, SCAN_T, 0, stream_>>>(count_, C, bsum_);
-        k_scan2<<<1, SCAN_T, 0, stream_>>>(bsum_, nb, cell_start_, C);
-        k_scan3<<<nb, SCAN_T, 0, stream_>>>(count_, C, bsum_, cell_start_);
-        k_scatter<<<blocks(n_), 256, 0, stream_>>>(n_, key_tmp_, rank_, cell_start_, id_[cur_],
-                                                   src_, sid_);
-        k_cellfix<<<blocks(C), 256, 0, stream_>>>(C, cell_start_, src_, sid_);
-        const int nxt = cur_ ^ 1;
-        GatherArgs<P> ga;
-        ga.n = n_;
-        ga.lam_dt = (real)(cfg_.lambda * cfg_.dt);
-        ga.src = src_;
-        ga.sid = sid_;
-        ga.pos_tmp = pos_tmp_;
-        ga.vel_old = vel_[cur_];
-        ga.frc_old = frc_[cur_];
-        ga.key_tmp = key_tmp_;
-        ga.pos = pos_;
-        ga.vel = vel_[nxt];
-        ga.frc = frc_[nxt];
-        ga.vt = vt_;
-        ga.key = key_;
-        ga.id = id_[nxt];
-        ga.inv_perm = inv_perm_;
-        k_gather<P><<<blocks(n_), 256, 0, stream_>>>(ga);
-        launches_ += 6;
-        cur_ = nxt;
-        DPD_CU(cudaGetLastError());
-        return DPD_OK;
-    }
-
-    // bonds (+ velocity update unless init) (+ reductions if sampled)
-    int enqueue_bonds(bool init, bool sample, bool accumulate) {
-        BondArgs<P> ba;
-        ba.n = n_;
-        ba.g = geo_;
-        for (int k = 0; k < 3; ++k) {
-            ba.L[k] = (real)geo_.L[k];
-            ba.h[k] = (real)geo_.h[k];
-        }
-        ba.half_dt = (real)(0.5 * cfg_.dt);
-        ba.fpair = fpair_;
-        ba.pos = pos_;
-        ba.key = key_;
-        ba.id = id_[cur_];
-        ba.inv_perm = inv_perm_;
-        ba.bptr = bptr_;
-        ba.bpartner = bpartner_;
-        ba.bpar = bpar_;
-        ba.vel = vel_[cur_];
-        ba.frc = frc_[cur_];
-        ba.ev = ev_;
-        if (init) {
-            if (sample) k_bond_vel<P, true, true><<<blocks(n_), 256, 0, stream_>>>(ba);
-            else k_bond_vel<P, true, false><<<blocks(n_), 256, 0, stream_>>>(ba);
-        } else {
-            if (sample) k_bond_vel<P, false, true><<<blocks(n_), 256, 0, stream_>>>(ba);
-            else k_bond_vel<P, false, false><<<blocks(n_), 256, 0, stream_>>>(ba);
-        }
-        ++launches_;
-        DPD_CU(cudaGetLastError());
-        if (sample) {
-            k_reduce<P><<<RED_BLOCKS, RED_T, 0, stream_>>>(n_, vel_[cur_], ev_, partial_);
-            const double V = geo_.L[0] * geo_.L[1] * geo_.L[2];
-            k_reduce_final<<<1, 32, 0, stream_>>>(RED_BLOCKS, partial_, obs_, acc_,
-                                                  accumulate ? 1 : 0,
-                                                  n_ > 1 ? 1.0 / (3.0 * n_ - 3.0) : 0.0,
-                                                  1.0 / (3.0 * V), status_);
-            launches_ += 2;
-            DPD_CU(cudaGetLastError());
-        }
-        return DPD_OK;
-    }
-
-    int enqueue_step(bool sample, bool accumulate, bool capturing = false) {
-        int rc = mark(0, capturing);
-        if (rc) return rc;
-        UpdArgs<P> ua;
-        ua.n = n_;
-        ua.g = geo_;
-        ua.dt = (real)cfg_.dt;
-        ua.half_dt2 = (real)(0.5 * cfg_.dt * cfg_.dt);
-        for (int k = 0; k < 3; ++k) {
-            ua.hf[k] = (float)geo_.h[k];
-            ua.inv_hf[k] = (float)geo_.inv_h[k];
-        }
-        ua.key = key_;
-        ua.pos = pos_;
-        ua.vel = vel_[cur_];
-        ua.frc = frc_[cur_];
-        ua.pos_tmp = pos_tmp_;
-        ua.key_tmp = key_tmp_;
-        ua.rank = rank_;
-        ua.count = count_;
-        ua.counter = counter_;
-        ua.status = status_;
-        k_update<P><<<blocks(n_), 256, 0, stream_>>>(ua);
-        ++launches_;
-        DPD_CU(cudaGetLastError());
-        if ((rc = enqueue_sort()) || (rc = mark(1, capturing)) || (rc = launch_pair(sample)) ||
-            (rc = mark(2, capturing)) || (rc = enqueue_bonds(false, sample, accumulate)))
-            return rc;
-        return mark(3, capturing);
-    }
-
 
     // One captured step per (parity, variant): the ping-pong buffers swap
-    // every step, so a graph is valid for the parity it was captured at.
+    // every step, so a graph is valid for the parity it was captured at; any
+    // change of the pools' membership drops the graphs.
     int launch_graph(int variant) {
         GraphSlot &g = graphs_[cur_][variant];
         if (!g.exec) {
@@ -624,6 +885,7 @@ class Engine : public EngineBase {
             DPD_CU(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal));
             int rc = enqueue_step(variant >= 1, variant == 2, true);
             cudaError_t e = cudaStreamEndCapture(stream_, &graph);
+            cur_ = cur0;   // capture did not execute anything
             if (rc) {
                 if (graph) cudaGraphDestroy(graph);
                 return rc;
@@ -655,7 +917,6 @@ class Engine : public EngineBase {
             }
             g.nkernels = launches_ - l0;
             launches_ = l0;
-            cur_ = cur0;   // capture did not execute anything
         }
         const bool timed = prof_on_ && prof_n_ < prof_max_;
         if (timed || g.timed) {
@@ -669,31 +930,37 @@ class Engine : public EngineBase {
         return DPD_OK;
     }
 
-    Config cfg_;
-    Geo geo_{};
-    int n_ = 0;
+    BatchConfig bc_;
+    int NB_ = 0, NC_ = 0, NBR_ = 0, NBD_ = 0, NS_ = 0, NRB_ = 0, T_ = 128;
     cudaStream_t stream_ = nullptr;
     bool own_stream_ = false;
     std::vector<void *> allocs_;
+    std::vector<SysHost> hs_;
+    std::vector<SysDesc<P>> hsys_;
+    std::vector<int> order_;               // live systems in pool order
+    int used_beads_ = 0, used_cells_ = 0, used_bricks_ = 0, used_bonds_ = 0;
+    int nred_all_ = 0, nrsys_all_ = 0;
+    int capmax_ = 0, xmax_ = 0;
+    size_t smem_ = 0;
     vec4 *pos_ = nullptr, *pos_tmp_ = nullptr, *vel_[2] = {nullptr, nullptr},
          *frc_[2] = {nullptr, nullptr}, *vt_ = nullptr, *fpair_ = nullptr, *ev_ = nullptr;
     uint32_t *key_ = nullptr, *key_tmp_ = nullptr, *rank_ = nullptr, *src_ = nullptr;
     int32_t *sid_ = nullptr, *id_[2] = {nullptr, nullptr}, *inv_perm_ = nullptr;
+    int *bsys_ = nullptr, *brick_sys_ = nullptr, *old_bead0_ = nullptr;
     uint32_t *count_ = nullptr, *cell_start_ = nullptr, *bsum_ = nullptr;
+    SysDesc<P> *sys_ = nullptr;
     long long *counter_ = nullptr;
     int *status_ = nullptr;
-    double *partial_ = nullptr, *obs_ = nullptr, *acc_ = nullptr, *io_ = nullptr;
-    void *io_host_ = nullptr;
-    int32_t *types_ = nullptr, *bptr_ = nullptr, *bpartner_ = nullptr;
+    real *atab_ = nullptr;
+    int32_t *bptr_ = nullptr, *bpartner_ = nullptr;
     vec4 *bpar_ = nullptr;
-    real *a_ = nullptr;
+    int2 *rmap_ = nullptr;
+    int4 *rsys_ = nullptr;
+    double *partial_ = nullptr, *obs_ = nullptr, *acc_ = nullptr, *io_ = nullptr;
+    size_t io_n_ = 0;
     int cur_ = 0;
-    bool has_state_ = false;
-    int64_t host_step_ = 0;
     int64_t launches_ = 0;
     int status_host_ = 0;
-    int T_ = 128, X_ = 1, BY_ = 2, BZ_ = 2, nbx_ = 1, nby_ = 1, nbz_ = 1, nseg_ = 1, cap_ = 256;
-    size_t smem_ = 0;
     GraphSlot graphs_[2][3];
     cudaEvent_t ph_[4] = {nullptr, nullptr, nullptr, nullptr};
     std::vector<cudaEvent_t> prof_ev_;

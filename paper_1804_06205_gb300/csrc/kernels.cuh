@@ -1,10 +1,18 @@
-// Device code of the DPD step loop (arxiv 1804.06205, Fig. 1) for sm_103a and
-// the per-precision engine that sequences it.  Included by engine_f32.cu and
-// engine_f64.cu, each of which instantiates one precision.
+// Device code of the DPD step loop (arxiv 1804.06205, Fig. 1) for sm_103a.
+// Included by engine_f32.cu and engine_f64.cu (one precision each) and by
+// cells_noalloc.cu (cell keys and scans only).
+//
+// Every kernel works on any number of resident systems at once: the systems
+// are packed one after another in shared bead, cell, brick and bond pools, a
+// per-system descriptor (SysDesc) holds geometry and parameters, and each
+// bead (bsys) and pair-kernel brick (brick_sys) names its system.  Because
+// the packing is contiguous in beads and cells alike, one global counting
+// sort orders all systems at once.  Ids, cell keys and Philox counters are
+// local to a system, so a system computes the same numbers alone or packed.
 //
 // One step (Fig. 1), all on the device:
-//   k_update      1.-2. r += dt v + dt^2/2 f, periodic wrap in FP64, new cell
-//                 key, histogram of cell occupancy (atomics on counts)
+//   k_update      1.-2. r += dt v + dt^2/2 f, periodic wrap, new cell key,
+//                 cell occupancy histogram (atomics on counts)
 //   k_scan*       3.    exclusive scan of the counts -> cell_start
 //   k_scatter     3.    slot = cell_start[key] + arrival rank
 //   k_cellfix     3.    canonical (cell, id) order inside each cell
@@ -99,6 +107,16 @@ __device__ __forceinline__ double u01_f64(uint32_t x) {
     return (double)((x >> 8) | 1u) * 0x1p-24;
 }
 
+// Explicitly rounded arithmetic for the force terms: every kernel variant
+// (sampled or not, initial or not) must produce the same bits, so the
+// compiler may not fuse these differently from one variant to another.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
 
@@ -158,41 +176,49 @@ __device__ __forceinline__ void decode_key(uint32_t k, const Geo &g, int &cx, in
 }
 
 // --------------------------------------------------------------------------
+// Per-system descriptor.
+// --------------------------------------------------------------------------
+template <class P>
+struct SysDesc {
+    using real = typename P::real;
+    int n, bead0, cell0, ncell;      // beads [bead0, bead0+n), cells [cell0, cell0+ncell)
+    int nx, ny, nz, ntypes;
+    int brick0, X, BY, BZ;           // pair-kernel bricks [brick0, brick0 + nbx*nby*nbz)
+    int nbx, nby, nbz, cap;          // cap: staged beads per brick chunk
+    int a_off, noise, pad0, pad1;    // a_ij table offset, noise kind
+    double L[3], h[3], inv_h[3];
+    float hf[3], inv_hf[3];          // FP32 cell edges (offset path)
+    real dt, half_dt2, half_dt, lam_dt, gamma, sig_sqdt;
+    uint32_t rk[20];                 // Philox round keys
+};
+
+__device__ __forceinline__ void decode_key3(uint32_t k, int nx, int ny, int &cx, int &cy, int &cz) {
+    cx = (int)(k % (uint32_t)nx);
+    const uint32_t q = k / (uint32_t)nx;
+    cy = (int)(q % (uint32_t)ny);
+    cz = (int)(q / (uint32_t)ny);
+}
+
+// --------------------------------------------------------------------------
 // a1-a2: position update, wrap, key (and set_state's initial binning).
 // --------------------------------------------------------------------------
 template <class P>
-struct UpdArgs {
-    using vec4 = typename P::vec4;
-    using real = typename P::real;
-    int n;
-    Geo g;
-    real dt, half_dt2;
-    float hf[3], inv_hf[3];   // cell edges in FP32 (offset path)
-    const uint32_t *key;
-    const vec4 *pos, *vel, *frc;
-    vec4 *pos_tmp;
-    uint32_t *key_tmp, *rank, *count;
-    long long *counter;
-    int *status;
-};
-
-template <class P>
-__device__ __forceinline__ void place_bead(const Geo &g, double x, double y, double z,
+__device__ __forceinline__ void place_bead(const SysDesc<P> &D, double x, double y, double z,
                                            typename P::real type, typename P::vec4 &out,
                                            uint32_t &key, int *status, int bad_bit) {
     using real = typename P::real;
     if (!(isfinite(x) && isfinite(y) && isfinite(z))) atomicOr(status, bad_bit);
-    x = wrap_fast(x, g.L[0]);
-    y = wrap_fast(y, g.L[1]);
-    z = wrap_fast(z, g.L[2]);
-    const int cx = cell_of(x, g.inv_h[0], g.nx);
-    const int cy = cell_of(y, g.inv_h[1], g.ny);
-    const int cz = cell_of(z, g.inv_h[2], g.nz);
-    key = ((uint32_t)cz * (uint32_t)g.ny + (uint32_t)cy) * (uint32_t)g.nx + (uint32_t)cx;
+    x = wrap_fast(x, D.L[0]);
+    y = wrap_fast(y, D.L[1]);
+    z = wrap_fast(z, D.L[2]);
+    const int cx = cell_of(x, D.inv_h[0], D.nx);
+    const int cy = cell_of(y, D.inv_h[1], D.ny);
+    const int cz = cell_of(z, D.inv_h[2], D.nz);
+    key = ((uint32_t)cz * (uint32_t)D.ny + (uint32_t)cy) * (uint32_t)D.nx + (uint32_t)cx;
     if (P::kOffsets) {
-        out = mk4<typename P::vec4, real>((real)(x - (double)cx * g.h[0]),
-                                          (real)(y - (double)cy * g.h[1]),
-                                          (real)(z - (double)cz * g.h[2]), type);
+        out = mk4<typename P::vec4, real>((real)(x - (double)cx * D.h[0]),
+                                          (real)(y - (double)cy * D.h[1]),
+                                          (real)(z - (double)cz * D.h[2]), type);
     } else {
         out = mk4<typename P::vec4, real>((real)x, (real)y, (real)z, type);
     }
@@ -217,47 +243,65 @@ __device__ __forceinline__ int move_cell(float &o, float h, float inv_h, int c, 
 }
 
 template <class P>
+struct UpdArgs {
+    using vec4 = typename P::vec4;
+    int b_lo, b_hi;
+    const SysDesc<P> *sys;
+    const int *bsys;
+    const uint32_t *key;             // local cell keys
+    const vec4 *pos, *vel, *frc;
+    vec4 *pos_tmp;
+    uint32_t *key_tmp, *rank, *count;
+    long long *counter;              // per system
+    int *status;
+};
+
+template <class P>
 __global__ void __launch_bounds__(256) k_update(UpdArgs<P> a) {
     using real = typename P::real;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t == 0) *a.counter += 1;   // evaluation counter of this step's force
-    if (t >= a.n) return;
+    const int t = a.b_lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.b_hi) return;
+    const int s = a.bsys[t];
+    const SysDesc<P> &D = a.sys[s];
+    if (t == D.bead0) a.counter[s] += 1;   // evaluation counter of this step's force
     const typename P::vec4 p = a.pos[t], v = a.vel[t], f = a.frc[t];
-    const real ddx = a.dt * v.x + a.half_dt2 * f.x;
-    const real ddy = a.dt * v.y + a.half_dt2 * f.y;
-    const real ddz = a.dt * v.z + a.half_dt2 * f.z;
+    const real dt = D.dt, hdt2 = D.half_dt2;
+    const real ddx = dt * v.x + hdt2 * f.x;
+    const real ddy = dt * v.y + hdt2 * f.y;
+    const real ddz = dt * v.z + hdt2 * f.z;
     typename P::vec4 out;
     uint32_t key;
     if (P::kOffsets) {
         int cx, cy, cz;
-        decode_key(a.key[t], a.g, cx, cy, cz);
+        decode_key3(a.key[t], D.nx, D.ny, cx, cy, cz);
         float ox = (float)p.x + (float)ddx, oy = (float)p.y + (float)ddy, oz = (float)p.z + (float)ddz;
         if (!(isfinite(ox) && isfinite(oy) && isfinite(oz))) {
             atomicOr(a.status, ST_NONFINITE);
             ox = oy = oz = 0.0f;
         }
-        cx = move_cell(ox, a.hf[0], a.inv_hf[0], cx, a.g.nx);
-        cy = move_cell(oy, a.hf[1], a.inv_hf[1], cy, a.g.ny);
-        cz = move_cell(oz, a.hf[2], a.inv_hf[2], cz, a.g.nz);
-        key = ((uint32_t)cz * (uint32_t)a.g.ny + (uint32_t)cy) * (uint32_t)a.g.nx + (uint32_t)cx;
+        cx = move_cell(ox, D.hf[0], D.inv_hf[0], cx, D.nx);
+        cy = move_cell(oy, D.hf[1], D.inv_hf[1], cy, D.ny);
+        cz = move_cell(oz, D.hf[2], D.inv_hf[2], cz, D.nz);
+        key = ((uint32_t)cz * (uint32_t)D.ny + (uint32_t)cy) * (uint32_t)D.nx + (uint32_t)cx;
         out = mk4<typename P::vec4, real>((real)ox, (real)oy, (real)oz, p.w);
     } else {
-        place_bead<P>(a.g, (double)p.x + (double)ddx, (double)p.y + (double)ddy,
+        place_bead<P>(D, (double)p.x + (double)ddx, (double)p.y + (double)ddy,
                       (double)p.z + (double)ddz, p.w, out, key, a.status, ST_NONFINITE);
     }
     a.pos_tmp[t] = out;
     a.key_tmp[t] = key;
-    a.rank[t] = atomicAdd(&a.count[key], 1u);
+    a.rank[t] = atomicAdd(&a.count[D.cell0 + key], 1u);
 }
 
+// set_state of one system: host positions/velocities in bead-id order
 template <class P>
 struct InitArgs {
     using vec4 = typename P::vec4;
-    int n;
-    Geo g;
+    int s;
+    const SysDesc<P> *sys;
     const double *pos_in, *vel_in;   // [n*3] bead-id order
-    const int32_t *types;
-    vec4 *pos_tmp, *vel, *frc;
+    const int32_t *types;            // [n]
+    vec4 *pos_tmp, *vel, *frc;       // at slots bead0 + id
     uint32_t *key_tmp, *rank, *count;
     int32_t *id;
     int *status;
@@ -266,20 +310,22 @@ struct InitArgs {
 template <class P>
 __global__ void __launch_bounds__(256) k_init(InitArgs<P> a) {
     using real = typename P::real;
+    const SysDesc<P> &D = a.sys[a.s];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
+    if (i >= D.n) return;
+    const int t = D.bead0 + i;
     typename P::vec4 out;
     uint32_t key;
-    place_bead<P>(a.g, a.pos_in[3 * i], a.pos_in[3 * i + 1], a.pos_in[3 * i + 2],
+    place_bead<P>(D, a.pos_in[3 * i], a.pos_in[3 * i + 1], a.pos_in[3 * i + 2],
                   (real)a.types[i], out, key, a.status, ST_BADINPUT);
-    a.pos_tmp[i] = out;
-    a.key_tmp[i] = key;
-    a.rank[i] = atomicAdd(&a.count[key], 1u);
+    a.pos_tmp[t] = out;
+    a.key_tmp[t] = key;
+    a.rank[t] = atomicAdd(&a.count[D.cell0 + key], 1u);
     const double vx = a.vel_in[3 * i], vy = a.vel_in[3 * i + 1], vz = a.vel_in[3 * i + 2];
     if (!(isfinite(vx) && isfinite(vy) && isfinite(vz))) atomicOr(a.status, ST_BADINPUT);
-    a.vel[i] = mk4<typename P::vec4, real>((real)vx, (real)vy, (real)vz, (real)0);
-    a.frc[i] = mk4<typename P::vec4, real>((real)0, (real)0, (real)0, (real)0);
-    a.id[i] = i;
+    a.vel[t] = mk4<typename P::vec4, real>((real)vx, (real)vy, (real)vz, (real)0);
+    a.frc[t] = mk4<typename P::vec4, real>((real)0, (real)0, (real)0, (real)0);
+    a.id[t] = i;
 }
 
 // --------------------------------------------------------------------------
@@ -366,23 +412,52 @@ static __global__ void __launch_bounds__(SCAN_T) k_scan3(uint32_t *count, int nc
         }
 }
 
-static __global__ void __launch_bounds__(256) k_scatter(int n, const uint32_t *key_tmp,
-                                                 const uint32_t *rank, const uint32_t *cell_start,
-                                                 const int32_t *id_old, uint32_t *src,
-                                                 int32_t *sid) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const uint32_t slot = cell_start[key_tmp[t]] + rank[t];
-    src[slot] = (uint32_t)t;
-    sid[slot] = id_old[t];
+// The same scans with the starts offset by `base` (the first bead slot of the
+// cell range being sorted).
+static __global__ void __launch_bounds__(SCAN_T) k_scan2b(uint32_t *bsum, int nb,
+                                                   uint32_t *cell_start, int ncell,
+                                                   uint32_t base) {
+    __shared__ uint32_t tot;
+    uint32_t carry = base;
+    for (int b0 = 0; b0 < nb; b0 += SCAN_T) {
+        const int b = b0 + threadIdx.x;
+        const uint32_t v = b < nb ? bsum[b] : 0u;
+        const uint32_t ex = block_excl_scan(v, &tot);
+        if (b < nb) bsum[b] = carry + ex;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) cell_start[ncell] = carry;
+}
+
+template <class P>
+struct ScatterArgs {
+    int b_lo, b_hi;
+    const SysDesc<P> *sys;
+    const int *bsys;
+    const uint32_t *key_tmp, *rank, *cell_start;
+    const int32_t *id_old;
+    uint32_t *src;
+    int32_t *sid;
+};
+
+template <class P>
+__global__ void __launch_bounds__(256) k_scatter(ScatterArgs<P> a) {
+    const int t = a.b_lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.b_hi) return;
+    const int s = a.bsys[t];
+    const uint32_t slot = a.cell_start[a.sys[s].cell0 + a.key_tmp[t]] + a.rank[t];
+    a.src[slot] = (uint32_t)t;
+    a.sid[slot] = a.id_old[t];
 }
 
 // Atomic ranks give an arbitrary order inside a cell; sort each cell's
 // entries by bead id (cells hold ~3 beads: insertion sort).
-static __global__ void __launch_bounds__(256) k_cellfix(int ncell, const uint32_t *cell_start,
-                                                 uint32_t *src, int32_t *sid) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
+static __global__ void __launch_bounds__(256) k_cellfix(int c_lo, int c_hi,
+                                                 const uint32_t *cell_start, uint32_t *src,
+                                                 int32_t *sid) {
+    const int c = c_lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= c_hi) return;
     const int b = (int)cell_start[c], e = (int)cell_start[c + 1];
     for (int i = b + 1; i < e; ++i) {
         const int32_t ki = sid[i];
@@ -401,9 +476,9 @@ static __global__ void __launch_bounds__(256) k_cellfix(int ncell, const uint32_
 template <class P>
 struct GatherArgs {
     using vec4 = typename P::vec4;
-    using real = typename P::real;
-    int n;
-    real lam_dt;
+    int b_lo, b_hi;
+    const SysDesc<P> *sys;
+    const int *bsys;
     const uint32_t *src;
     const int32_t *sid;
     const vec4 *pos_tmp, *vel_old, *frc_old;
@@ -415,20 +490,22 @@ struct GatherArgs {
 
 template <class P>
 __global__ void __launch_bounds__(256) k_gather(GatherArgs<P> a) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.n) return;
+    const int t = a.b_lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.b_hi) return;
+    const SysDesc<P> &D = a.sys[a.bsys[t]];
     const uint32_t s = a.src[t];
     const int32_t i = a.sid[t];
     const typename P::vec4 v = a.vel_old[s], f = a.frc_old[s];
+    const typename P::real lam_dt = D.lam_dt;
     a.pos[t] = a.pos_tmp[s];
     a.key[t] = a.key_tmp[s];
     a.vel[t] = v;
     a.frc[t] = f;
     a.id[t] = i;
-    a.inv_perm[i] = t;
+    a.inv_perm[D.bead0 + i] = t;
     // Fig. 1 step 2: velocity predictor used by the dissipative force
-    a.vt[t] = mk4<typename P::vec4, typename P::real>(v.x + a.lam_dt * f.x, v.y + a.lam_dt * f.y,
-                                                      v.z + a.lam_dt * f.z, P::pack_id(i));
+    a.vt[t] = mk4<typename P::vec4, typename P::real>(v.x + lam_dt * f.x, v.y + lam_dt * f.y,
+                                                      v.z + lam_dt * f.z, P::pack_id(i));
 }
 
 // --------------------------------------------------------------------------
@@ -457,22 +534,36 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs<P> a) {
 // frame coordinates.
 // --------------------------------------------------------------------------
 template <class P>
-struct PairArgs {
+struct PairArgs {   // one brick's system, as the kernel body uses it
     using vec4 = typename P::vec4;
     using real = typename P::real;
     const vec4 *pos, *vt;
-    const uint32_t *key, *cell_start;
+    const uint32_t *key, *cell_start;   // cell_start offset to the system's cells
     vec4 *fpair, *ev;
-    const real *a;
+    const real *a;                      // the system's a_ij table
     int ntypes;
     int nx, ny, nz;
-    int X, BY, BZ, nbx, nby;          // brick shape, bricks along x and y
+    int X, BY, BZ, nbx, nby;
     real h[3];
     real gamma, sig_sqdt;
-    uint32_t rk[20];                  // Philox round keys k + r (W0, W1)
     int noise;
     const long long *counter;
     int cap;
+};
+
+template <class P>
+struct PairLaunch {   // a launch over bricks [br_lo, br_lo + gridDim.x) of any systems
+    using vec4 = typename P::vec4;
+    using real = typename P::real;
+    const SysDesc<P> *sys;
+    const int *brick_sys;
+    int br_lo;
+    int capmax, Xmax;                   // shared-memory layout
+    const vec4 *pos, *vt;
+    const uint32_t *key, *cell_start;
+    vec4 *fpair, *ev;
+    const real *atab;
+    const long long *counter;
 };
 
 constexpr int PAIR_MAXX = 64;          // largest brick length (cells)
@@ -530,18 +621,50 @@ __device__ __forceinline__ double theta_pair(uint2 x, int noise, double) {
 }
 
 template <class P, int T, bool SAMPLE>
-__global__ void __launch_bounds__(T) k_pair(PairArgs<P> a) {
+__global__ void __launch_bounds__(T) k_pair(PairLaunch<P> la) {
     using real = typename P::real;
     using vec4 = typename P::vec4;
     constexpr int NW = T / 32;
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(32) unsigned char smem[];
-    const int cap = a.cap;
+    // this block's brick and system
+    const int brick = la.br_lo + blockIdx.x;
+    const int sysi = la.brick_sys[brick];
+    const SysDesc<P> &D = la.sys[sysi];
+    PairArgs<P> a;
+    a.pos = la.pos;
+    a.vt = la.vt;
+    a.key = la.key;
+    a.cell_start = la.cell_start + D.cell0;
+    a.fpair = la.fpair;
+    a.ev = la.ev;
+    a.a = la.atab + D.a_off;
+    a.ntypes = D.ntypes;
+    a.nx = D.nx;
+    a.ny = D.ny;
+    a.nz = D.nz;
+    a.X = D.X;
+    a.BY = D.BY;
+    a.BZ = D.BZ;
+    a.nbx = D.nbx;
+    a.nby = D.nby;
+    a.h[0] = (real)D.h[0];
+    a.h[1] = (real)D.h[1];
+    a.h[2] = (real)D.h[2];
+    a.gamma = D.gamma;
+    a.sig_sqdt = D.sig_sqdt;
+    uint32_t rkl[20];   // block-uniform round keys
+#pragma unroll
+    for (int r = 0; r < 20; ++r) rkl[r] = D.rk[r];
+    a.noise = D.noise;
+    a.counter = la.counter + sysi;
+    a.cap = la.capmax;
+    const int cap = la.capmax;
     const int X = a.X;
     vec4 *s_pos = reinterpret_cast<vec4 *>(smem);
     vec4 *s_vt = s_pos + cap;
     int *s_cs = reinterpret_cast<int *>(s_vt + cap);
-    int *s_pc = s_cs + PAIR_NR * (X + 3);
+    int *s_pc = s_cs + PAIR_NR * (la.Xmax + 3);
     int *s_hr = s_pc + PAIR_NR * 3 * PAIR_PC;        // home rows: staged row, first, count, global
     size_t off = PairSmem<P>::align16((size_t)((unsigned char *)(s_hr + 16) - smem));
     real *s_a = reinterpret_cast<real *>(smem + off);
@@ -554,7 +677,7 @@ __global__ void __launch_bounds__(T) k_pair(PairArgs<P> a) {
     uint32_t *s_q = reinterpret_cast<uint32_t *>(s_acce + NW * 32);
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    int bid = blockIdx.x;
+    int bid = brick - D.brick0;
     const int bx = bid % a.nbx;
     bid /= a.nbx;
     const int byi = bid % a.nby, bzi = bid / a.nby;
@@ -766,7 +889,7 @@ __global__ void __launch_bounds__(T) k_pair(PairArgs<P> a) {
                         for (; q < qe; ++q) {
                             const vec4 pj = s_pos[q - c0];
                             const real dx = xi - pj.x, dyv = yi - pj.y, dzv = zi - pj.z;
-                            const real r2 = dx * dx + dyv * dyv + dzv * dzv;
+                            const real r2 = fma_rn(dzv, dzv, fma_rn(dyv, dyv, mul_rn(dx, dx)));
                             if (r2 < (real)1 && r2 > (real)0) {
                                 my_q[nh * 32 + lane] = (uint32_t)(q - c0) | ((uint32_t)nh << 11) |
                                                        ((uint32_t)lane << 15);
@@ -804,22 +927,24 @@ __global__ void __launch_bounds__(T) k_pair(PairArgs<P> a) {
                         const vec4 hpo = my_hp[owner], hvo = my_hv[owner];
                         const vec4 pj = s_pos[jl], vj = s_vt[jl];
                         const real dx = hpo.x - pj.x, dyv = hpo.y - pj.y, dzv = hpo.z - pj.z;
-                        const real r2 = dx * dx + dyv * dyv + dzv * dzv;
+                        const real r2 = fma_rn(dzv, dzv, fma_rn(dyv, dyv, mul_rn(dx, dx)));
                         const real rinv = rsqrt_r(r2);
-                        const real rr1 = r2 * rinv;
+                        const real rr1 = mul_rn(r2, rinv);
                         const real w = (real)1 - rr1;
-                        const real ex = dx * rinv, ey = dyv * rinv, ez = dzv * rinv;
-                        const real evel = ex * (hvo.x - vj.x) + ey * (hvo.y - vj.y) + ez * (hvo.z - vj.z);
+                        const real ex = mul_rn(dx, rinv), ey = mul_rn(dyv, rinv), ez = mul_rn(dzv, rinv);
+                        const real evel = fma_rn(ez, hvo.z - vj.z,
+                                                 fma_rn(ey, hvo.y - vj.y, mul_rn(ex, hvo.x - vj.x)));
                         const real aij = s_a[(int)hpo.w * nt + (int)pj.w];
                         const int32_t idi = P::unpack_id(hvo.w), idj = P::unpack_id(vj.w);
                         const uint32_t lo = (uint32_t)min(idi, idj), hi = (uint32_t)max(idi, idj);
-                        const uint2 rnd = philox_rk(lo, hi, s_lo, s_hi, a.rk);
+                        const uint2 rnd = philox_rk(lo, hi, s_lo, s_hi, rkl);
                         const real th = theta_pair(rnd, a.noise, (real)0);
-                        const real fc = aij * w;
-                        const real mag = fc - a.gamma * w * w * evel + a.sig_sqdt * w * th;
-                        fx = mag * ex;
-                        fy = mag * ey;
-                        fz = mag * ez;
+                        const real fc = mul_rn(aij, w);
+                        const real gw2 = mul_rn(mul_rn(a.gamma, w), w);
+                        const real mag = fma_rn(mul_rn(a.sig_sqdt, w), th, fma_rn(-gw2, evel, fc));
+                        fx = mul_rn(mag, ex);
+                        fy = mul_rn(mag, ey);
+                        fz = mul_rn(mag, ez);
                         if (SAMPLE) {
                             wc = rr1 * fc;
                             ep = (real)0.5 * fc * w;
@@ -830,9 +955,9 @@ __global__ void __launch_bounds__(T) k_pair(PairArgs<P> a) {
                     for (int lv = lv_lo; lv <= lv_hi; ++lv) {
                         if (valid && lvl == lv) {
                             vec4 s = my_acc[owner];
-                            s.x += fx;
-                            s.y += fy;
-                            s.z += fz;
+                            s.x = add_rn(s.x, fx);
+                            s.y = add_rn(s.y, fy);
+                            s.z = add_rn(s.z, fz);
                             if (SAMPLE) {
                                 s.w += wc;
                                 my_acce[owner] += ep;
@@ -882,51 +1007,50 @@ __device__ __forceinline__ void bond_force(int kind, R r0, R k, R alpha, R dx, R
         U = k * (((R)1 - x) * ((R)1 - x) - (R)1);
         if (r > (R)0) coef = -(R)2 * k * alpha * x * ((R)1 - x) / r;
     }
-    fx = coef * dx;
-    fy = coef * dy;
-    fz = coef * dz;
+    fx = mul_rn(coef, dx);
+    fy = mul_rn(coef, dy);
+    fz = mul_rn(coef, dz);
 }
 
 template <class P>
 struct BondArgs {
     using vec4 = typename P::vec4;
-    using real = typename P::real;
-    int n;
-    Geo g;
-    real L[3], h[3];
-    real half_dt;
+    int b_lo, b_hi;
+    const SysDesc<P> *sys;
+    const int *bsys;
     const vec4 *fpair, *pos;
     const uint32_t *key;
     const int32_t *id, *inv_perm;
-    const int32_t *bptr, *bpartner;
+    const int32_t *bptr;   // [bead0 + id] -> first record (pool offset)
+    const int32_t *bpartner;   // partner's local id
     const vec4 *bpar;      // r0, k, alpha, kind
     vec4 *vel, *frc, *ev;
 };
 
 template <class P>
-__device__ __forceinline__ void bond_disp(const BondArgs<P> &a, int t, int u,
+__device__ __forceinline__ void bond_disp(const BondArgs<P> &a, const SysDesc<P> &D, int t, int u,
                                           typename P::real &dx, typename P::real &dy,
                                           typename P::real &dz) {
     using real = typename P::real;
     const typename P::vec4 pi = a.pos[t], pj = a.pos[u];
     if (P::kOffsets) {
         int xi, yi, zi, xj, yj, zj;
-        decode_key(a.key[t], a.g, xi, yi, zi);
-        decode_key(a.key[u], a.g, xj, yj, zj);
+        decode_key3(a.key[t], D.nx, D.ny, xi, yi, zi);
+        decode_key3(a.key[u], D.nx, D.ny, xj, yj, zj);
         int ddx = xi - xj, ddy = yi - yj, ddz = zi - zj;   // nearest periodic image in cells
-        if (2 * ddx > a.g.nx) ddx -= a.g.nx; else if (2 * ddx < -a.g.nx) ddx += a.g.nx;
-        if (2 * ddy > a.g.ny) ddy -= a.g.ny; else if (2 * ddy < -a.g.ny) ddy += a.g.ny;
-        if (2 * ddz > a.g.nz) ddz -= a.g.nz; else if (2 * ddz < -a.g.nz) ddz += a.g.nz;
-        dx = (pi.x - pj.x) + (real)ddx * a.h[0];
-        dy = (pi.y - pj.y) + (real)ddy * a.h[1];
-        dz = (pi.z - pj.z) + (real)ddz * a.h[2];
+        if (2 * ddx > D.nx) ddx -= D.nx; else if (2 * ddx < -D.nx) ddx += D.nx;
+        if (2 * ddy > D.ny) ddy -= D.ny; else if (2 * ddy < -D.ny) ddy += D.ny;
+        if (2 * ddz > D.nz) ddz -= D.nz; else if (2 * ddz < -D.nz) ddz += D.nz;
+        dx = (pi.x - pj.x) + (real)ddx * (real)D.h[0];
+        dy = (pi.y - pj.y) + (real)ddy * (real)D.h[1];
+        dz = (pi.z - pj.z) + (real)ddz * (real)D.h[2];
     } else {
         dx = pi.x - pj.x;
         dy = pi.y - pj.y;
         dz = pi.z - pj.z;
-        dx -= a.L[0] * rint(dx / a.L[0]);
-        dy -= a.L[1] * rint(dy / a.L[1]);
-        dz -= a.L[2] * rint(dz / a.L[2]);
+        dx -= (real)D.L[0] * rint(dx / (real)D.L[0]);
+        dy -= (real)D.L[1] * rint(dy / (real)D.L[1]);
+        dz -= (real)D.L[2] * rint(dz / (real)D.L[2]);
     }
 }
 
@@ -934,28 +1058,32 @@ template <class P, bool INIT, bool SAMPLE>
 __global__ void __launch_bounds__(256) k_bond_vel(BondArgs<P> a) {
     using real = typename P::real;
     using vec4 = typename P::vec4;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.n) return;
+    const int t = a.b_lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.b_hi) return;
+    const SysDesc<P> &D = a.sys[a.bsys[t]];
     const vec4 fp = a.fpair[t];
     real fx = fp.x, fy = fp.y, fz = fp.z, wb = 0, eb = 0;
     const int32_t i = a.id[t];
-    const int b0 = a.bptr[i], b1 = a.bptr[i + 1];
+    const int b0 = a.bptr[D.bead0 + i], b1 = a.bptr[D.bead0 + i + 1];
     for (int b = b0; b < b1; ++b) {
-        const int u = a.inv_perm[a.bpartner[b]];
+        const int u = a.inv_perm[D.bead0 + a.bpartner[b]];
         const vec4 bp = a.bpar[b];
         real dx, dy, dz, gx, gy, gz, U;
-        bond_disp<P>(a, t, u, dx, dy, dz);
+        bond_disp<P>(a, D, t, u, dx, dy, dz);
         bond_force<real>((int)bp.w, bp.x, bp.y, bp.z, dx, dy, dz, gx, gy, gz, U);
-        fx += gx; fy += gy; fz += gz;
+        fx = add_rn(fx, gx);
+        fy = add_rn(fy, gy);
+        fz = add_rn(fz, gz);
         if (SAMPLE) {
             wb += dx * gx + dy * gy + dz * gz;
             eb += U;
         }
     }
     if (!INIT) {
+        const real hdt = D.half_dt;
         const vec4 v = a.vel[t], f = a.frc[t];
-        a.vel[t] = mk4<vec4, real>(v.x + a.half_dt * (f.x + fx), v.y + a.half_dt * (f.y + fy),
-                                   v.z + a.half_dt * (f.z + fz), (real)0);
+        a.vel[t] = mk4<vec4, real>(v.x + hdt * (f.x + fx), v.y + hdt * (f.y + fy),
+                                   v.z + hdt * (f.z + fz), (real)0);
     }
     a.frc[t] = mk4<vec4, real>(fx, fy, fz, (real)0);
     if (SAMPLE) {
@@ -965,17 +1093,20 @@ __global__ void __launch_bounds__(256) k_bond_vel(BondArgs<P> a) {
 }
 
 // --------------------------------------------------------------------------
-// a8: FP64 reductions.  Pass 1: fixed grid, per-block partial sums of
-// (px, py, pz, v^2, wc, ep, wb, eb).  Pass 2: one block adds the partials in
-// block order (deterministic) and updates the running means.
+// a8: FP64 reductions, per system.  Pass 1: each block adds one chunk of one
+// system's beads, (px, py, pz, v^2, wc, ep, wb, eb).  Pass 2: one block per
+// system adds its chunks in order (deterministic) and updates its running
+// means.
 // --------------------------------------------------------------------------
-constexpr int RED_T = 256, RED_BLOCKS = 304, RED_K = 8;
+constexpr int RED_T = 256, RED_CHUNK = 4096, RED_K = 8;
 
+// rmap[block] = (first bead slot, end slot); rsys[k] = (system, first block, blocks)
 template <class P>
-__global__ void __launch_bounds__(RED_T) k_reduce(int n, const typename P::vec4 *vel,
+__global__ void __launch_bounds__(RED_T) k_reduce(const int2 *rmap, const typename P::vec4 *vel,
                                                   const typename P::vec4 *ev, double *partial) {
+    const int2 r = rmap[blockIdx.x];
     double s[RED_K] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int t = blockIdx.x * RED_T + threadIdx.x; t < n; t += gridDim.x * RED_T) {
+    for (int t = r.x + threadIdx.x; t < r.y; t += RED_T) {
         const typename P::vec4 v = vel[t], e = ev[t];
         const double vx = v.x, vy = v.y, vz = v.z;
         s[0] += vx; s[1] += vy; s[2] += vz;
@@ -999,104 +1130,118 @@ __global__ void __launch_bounds__(RED_T) k_reduce(int n, const typename P::vec4 
     }
 }
 
-// obs[0..7]: px, py, pz, sum v^2, W_C, E_pair, W_B, E_bond (pair/bond sums
-// halved: every pair / bond was visited from both ends).
-// acc[0..2]: sum of kT, sum of p_total, number of samples.
-static __global__ void k_reduce_final(int nblocks, const double *partial, double *obs, double *acc,
-                               int accumulate, double inv_3n3, double inv_3V, int *status) {
+// obs[s*8 + 0..7]: px, py, pz, sum v^2, W_C, E_pair, W_B, E_bond (pair/bond
+// sums halved: every pair / bond was visited from both ends).
+// acc[s*4 + 0..2]: sum of kT, sum of p_total, number of samples.
+template <class P>
+__global__ void k_reduce_final(const int4 *rsys, const SysDesc<P> *sys, const double *partial,
+                               double *obs, double *acc, int accumulate, int *status) {
+    const int4 q = rsys[blockIdx.x];
+    const int s = q.x;
     __shared__ double r[RED_K];
     if (threadIdx.x < RED_K) {
         double x = 0;
-        for (int b = 0; b < nblocks; ++b) x += partial[b * RED_K + threadIdx.x];
+        for (int b = q.y; b < q.y + q.z; ++b) x += partial[b * RED_K + threadIdx.x];
         r[threadIdx.x] = threadIdx.x >= 4 ? 0.5 * x : x;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         bool ok = true;
         for (int k = 0; k < RED_K; ++k) {
-            obs[k] = r[k];
+            obs[s * RED_K + k] = r[k];
             ok = ok && isfinite(r[k]);
         }
         if (!ok) atomicOr(status, ST_NONFINITE);
         if (accumulate) {
-            acc[0] += r[3] * inv_3n3;
-            acc[1] += (r[3] + r[4] + r[6]) * inv_3V;
-            acc[2] += 1.0;
+            const SysDesc<P> &D = sys[s];
+            const double V = D.L[0] * D.L[1] * D.L[2];
+            const double inv_3n3 = D.n > 1 ? 1.0 / (3.0 * D.n - 3.0) : 0.0;
+            acc[4 * s] += r[3] * inv_3n3;
+            acc[4 * s + 1] += (r[3] + r[4] + r[6]) / (3.0 * V);
+            acc[4 * s + 2] += 1.0;
         }
     }
 }
 
 // --------------------------------------------------------------------------
-// State read-back and the cell-division inspection.
+// State read-back and the cell-division inspection (one system).
 // --------------------------------------------------------------------------
 template <class P>
-__global__ void __launch_bounds__(256) k_unpermute(int n, Geo g, const typename P::vec4 *pos,
+__global__ void __launch_bounds__(256) k_unpermute(int s, const SysDesc<P> *sys,
+                                                   const typename P::vec4 *pos,
                                                    const uint32_t *key,
                                                    const typename P::vec4 *vel,
                                                    const typename P::vec4 *frc, const int32_t *id,
                                                    double *opos, double *ovel, double *ofrc) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
+    const SysDesc<P> &D = sys[s];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= D.n) return;
+    const int t = D.bead0 + k;
     const int i = id[t];
     const typename P::vec4 p = pos[t], v = vel[t], f = frc[t];
     double x = p.x, y = p.y, z = p.z;
     if (P::kOffsets) {
         int cx, cy, cz;
-        decode_key(key[t], g, cx, cy, cz);
-        x = wrap_fast((double)cx * g.h[0] + x, g.L[0]);
-        y = wrap_fast((double)cy * g.h[1] + y, g.L[1]);
-        z = wrap_fast((double)cz * g.h[2] + z, g.L[2]);
+        decode_key3(key[t], D.nx, D.ny, cx, cy, cz);
+        x = wrap_fast((double)cx * D.h[0] + x, D.L[0]);
+        y = wrap_fast((double)cy * D.h[1] + y, D.L[1]);
+        z = wrap_fast((double)cz * D.h[2] + z, D.L[2]);
     }
     opos[3 * i] = x; opos[3 * i + 1] = y; opos[3 * i + 2] = z;
     ovel[3 * i] = v.x; ovel[3 * i + 1] = v.y; ovel[3 * i + 2] = v.z;
     ofrc[3 * i] = f.x; ofrc[3 * i + 1] = f.y; ofrc[3 * i + 2] = f.z;
 }
 
-static __global__ void __launch_bounds__(256) k_cells_out(int n, const uint32_t *key, const int32_t *id,
+template <class P>
+__global__ void __launch_bounds__(256) k_cells_out(int s, const SysDesc<P> *sys,
+                                                   const uint32_t *key, const int32_t *id,
                                                    uint32_t *key_by_id, int64_t *order) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const int i = id[t];
-    key_by_id[i] = key[t];
-    order[t] = i;
+    const SysDesc<P> &D = sys[s];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= D.n) return;
+    const int i = id[D.bead0 + k];
+    key_by_id[i] = key[D.bead0 + k];
+    order[k] = i;
 }
 
 // g(r): unique pairs (slot j > slot i) within (2K+1)^3 cells, FP64 distances.
 template <class P>
-__global__ void __launch_bounds__(256) k_gr(int n, Geo g, int Kx, int Ky, int Kz,
+__global__ void __launch_bounds__(256) k_gr(int s, const SysDesc<P> *sys, int Kx, int Ky, int Kz,
                                             const typename P::vec4 *pos, const uint32_t *key,
                                             const uint32_t *cell_start, double rmax, double dr,
                                             int nbins, unsigned long long *counts) {
     extern __shared__ unsigned long long s_cnt[];
+    const SysDesc<P> &D = sys[s];
     for (int b = threadIdx.x; b < nbins; b += blockDim.x) s_cnt[b] = 0ull;
     __syncthreads();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < D.n) {
+        const int t = D.bead0 + k;
         int cx, cy, cz;
-        decode_key(key[t], g, cx, cy, cz);
+        decode_key3(key[t], D.nx, D.ny, cx, cy, cz);
         const typename P::vec4 pi = pos[t];
         for (int dz = -Kz; dz <= Kz; ++dz)
             for (int dy = -Ky; dy <= Ky; ++dy)
                 for (int dx = -Kx; dx <= Kx; ++dx) {
-                    const int xx = (cx + dx + 8 * g.nx) % g.nx;
-                    const int yy = (cy + dy + 8 * g.ny) % g.ny;
-                    const int zz = (cz + dz + 8 * g.nz) % g.nz;
-                    const uint32_t c = ((uint32_t)zz * g.ny + yy) * g.nx + xx;
+                    const int xx = (cx + dx + 8 * D.nx) % D.nx;
+                    const int yy = (cy + dy + 8 * D.ny) % D.ny;
+                    const int zz = (cz + dz + 8 * D.nz) % D.nz;
+                    const uint32_t c = D.cell0 + ((uint32_t)zz * D.ny + yy) * D.nx + xx;
                     const int b = (int)cell_start[c], e = (int)cell_start[c + 1];
                     for (int u = max(b, t + 1); u < e; ++u) {
                         const typename P::vec4 pj = pos[u];
                         double d[3];
                         if (P::kOffsets) {
-                            d[0] = ((double)pi.x - (double)pj.x) + (double)(-dx) * g.h[0];
-                            d[1] = ((double)pi.y - (double)pj.y) + (double)(-dy) * g.h[1];
-                            d[2] = ((double)pi.z - (double)pj.z) + (double)(-dz) * g.h[2];
+                            d[0] = ((double)pi.x - (double)pj.x) + (double)(-dx) * D.h[0];
+                            d[1] = ((double)pi.y - (double)pj.y) + (double)(-dy) * D.h[1];
+                            d[2] = ((double)pi.z - (double)pj.z) + (double)(-dz) * D.h[2];
                         } else {
                             const double pa[3] = {(double)pi.x, (double)pi.y, (double)pi.z};
                             const double pb[3] = {(double)pj.x, (double)pj.y, (double)pj.z};
 #pragma unroll
-                            for (int k = 0; k < 3; ++k) {
-                                const double dd = __dsub_rn(pa[k], pb[k]);
-                                d[k] = __dsub_rn(dd, __dmul_rn(g.L[k], rint(__ddiv_rn(dd, g.L[k]))));
+                            for (int q = 0; q < 3; ++q) {
+                                const double dd = __dsub_rn(pa[q], pb[q]);
+                                d[q] = __dsub_rn(dd, __dmul_rn(D.L[q], rint(__ddiv_rn(dd, D.L[q]))));
                             }
                         }
                         const double r = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]),
@@ -1112,6 +1257,38 @@ __global__ void __launch_bounds__(256) k_gr(int n, Geo g, int Kx, int Ky, int Kz
     __syncthreads();
     for (int b = threadIdx.x; b < nbins; b += blockDim.x)
         if (s_cnt[b]) atomicAdd(&counts[b], s_cnt[b]);
+}
+
+// --------------------------------------------------------------------------
+// Re-packing after a system left: every surviving bead moves from its old
+// slot (old bead0 of its system + its rank) to the new packed slot.
+// --------------------------------------------------------------------------
+template <class P>
+struct RelayoutArgs {
+    using vec4 = typename P::vec4;
+    int n_new;
+    const int *bsys_new;
+    const SysDesc<P> *sys_new;
+    const int *old_bead0;      // per system slot
+    const vec4 *pos, *vel, *frc;
+    const uint32_t *key;
+    const int32_t *id;
+    vec4 *pos_out, *vel_out, *frc_out;
+    uint32_t *key_out;
+    int32_t *id_out;
+};
+
+template <class P>
+__global__ void __launch_bounds__(256) k_relayout(RelayoutArgs<P> a) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.n_new) return;
+    const int s = a.bsys_new[t];
+    const int u = a.old_bead0[s] + (t - a.sys_new[s].bead0);
+    a.pos_out[t] = a.pos[u];
+    a.vel_out[t] = a.vel[u];
+    a.frc_out[t] = a.frc[u];
+    a.key_out[t] = a.key[u];
+    a.id_out[t] = a.id[u];
 }
 
 }  // namespace dpd

@@ -32,7 +32,10 @@ DPD_NOISE_UNIFORM = 1
 EXPORTED = ("dpd_default_options", "dpd_create", "dpd_set_state", "dpd_step", "dpd_get_state",
             "dpd_observables", "dpd_gr", "dpd_get_cells", "dpd_cell_dims", "dpd_sync",
             "dpd_launch_count", "dpd_profile_begin", "dpd_profile_end", "dpd_destroy",
-            "dpd_strerror", "dpd_last_error", "dpd_cells_noalloc")
+            "dpd_strerror", "dpd_last_error", "dpd_cells_noalloc", "dpd_batch_create",
+            "dpd_batch_add", "dpd_batch_remove", "dpd_batch_step", "dpd_batch_get_state",
+            "dpd_batch_observables", "dpd_batch_usage", "dpd_batch_sync", "dpd_batch_launch_count",
+            "dpd_batch_last_error", "dpd_batch_destroy")
 
 
 class dpd_box(C.Structure):
@@ -48,6 +51,11 @@ class dpd_options(C.Structure):
     _fields_ = [("lambda_", C.c_double), ("seed", C.c_uint64), ("precision", C.c_int32),
                 ("noise", C.c_int32), ("sample_every", C.c_int32), ("tile_cells", C.c_int32),
                 ("threads", C.c_int32), ("use_graph", C.c_int32), ("cuda_stream", C.c_void_p)]
+
+
+class dpd_batch_capacity(C.Structure):
+    _fields_ = [("max_beads", C.c_int64), ("max_cells", C.c_int64), ("max_bonds", C.c_int64),
+                ("max_systems", C.c_int32), ("pad", C.c_int32)]
 
 
 class dpd_obs(C.Structure):
@@ -97,6 +105,21 @@ def _load():
     lib.dpd_last_error.argtypes = [P]
     lib.dpd_last_error.restype = C.c_char_p
     lib.dpd_cells_noalloc.argtypes = [P, C.c_int64, P, P, P, P, P]
+    lib.dpd_batch_create.argtypes = [P, P, P]
+    lib.dpd_batch_add.argtypes = [P, P, C.c_int64, P, C.c_int32, P, C.c_double, C.c_double,
+                                  C.c_double, P, C.c_int64, P, C.c_int64, C.c_double, C.c_uint64,
+                                  P, P, C.c_int64, P]
+    lib.dpd_batch_remove.argtypes = [P, C.c_int32]
+    lib.dpd_batch_step.argtypes = [P, C.c_int64]
+    lib.dpd_batch_get_state.argtypes = [P, C.c_int32, P, P, P, P]
+    lib.dpd_batch_observables.argtypes = [P, C.c_int32, P]
+    lib.dpd_batch_usage.argtypes = [P, P, P, P]
+    lib.dpd_batch_sync.argtypes = [P]
+    lib.dpd_batch_launch_count.argtypes = [P]
+    lib.dpd_batch_launch_count.restype = C.c_int64
+    lib.dpd_batch_last_error.argtypes = [P]
+    lib.dpd_batch_last_error.restype = C.c_char_p
+    lib.dpd_batch_destroy.argtypes = [P]
     return lib
 
 
@@ -259,3 +282,98 @@ class System:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """Many independent systems advanced by the same launches (dpd_batch_*)."""
+
+    def __init__(self, max_beads, max_cells, max_bonds=0, max_systems=64, options=None, **opt):
+        self.h = C.c_void_p()
+        cap = dpd_batch_capacity(int(max_beads), int(max_cells), int(max_bonds),
+                                 int(max_systems), 0)
+        if options is None:
+            options = default_options(**opt)
+        self.options = options
+        rc = lib.dpd_batch_create(C.byref(cap), C.byref(options), C.byref(self.h))
+        if rc != DPD_OK:
+            raise DPDError(rc, "dpd_batch_create", lib.dpd_batch_last_error(None).decode())
+        self.n = {}
+
+    def _check(self, rc, where):
+        if rc != DPD_OK:
+            raise DPDError(rc, where, lib.dpd_batch_last_error(self.h).decode())
+
+    def try_add(self, L, types, a, gamma, kT, dt, pos, vel, bonds=None, morse=None, lam=0.65,
+                seed=0, step=0):
+        """Add a system with its state; returns its index, or None when it does
+        not fit in the pools (DPD_ENOMEM: not admitted)."""
+        L = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,))
+        box = dpd_box((C.c_double * 3)(*L))
+        types = np.ascontiguousarray(types, dtype=np.int32)
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        ntypes = int(round(np.sqrt(a.size)))
+        empty = dict(i=[], j=[], kind=[], r0=[], k=[], alpha=[])
+        brec, nb = _records_fast(bonds if bonds is not None else empty)
+        mrec, nm = _records_fast(morse if morse is not None else empty)
+        pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(types.size, 3)
+        vel = np.ascontiguousarray(vel, dtype=np.float64).reshape(types.size, 3)
+        sys_ = C.c_int32(-1)
+        rc = lib.dpd_batch_add(self.h, C.byref(box), int(types.size), _ptr(types), ntypes,
+                               _ptr(a), float(gamma), float(kT), float(dt), _ptr(brec), nb,
+                               _ptr(mrec), nm, float(lam), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                               _ptr(pos), _ptr(vel), int(step), C.byref(sys_))
+        if rc == DPD_ENOMEM:
+            return None
+        self._check(rc, "dpd_batch_add")
+        self.n[sys_.value] = int(types.size)
+        return sys_.value
+
+    def add_workload(self, w, step=0):
+        return self.try_add(w.L, w.types, w.a, w.gamma, w.kT, w.dt, w.pos, w.vel,
+                            bonds=w.bonds, lam=w.lam, seed=w.seed, step=step)
+
+    def remove(self, s):
+        self._check(lib.dpd_batch_remove(self.h, int(s)), "dpd_batch_remove")
+        self.n.pop(s, None)
+
+    def step(self, nsteps=1):
+        self._check(lib.dpd_batch_step(self.h, int(nsteps)), "dpd_batch_step")
+
+    def get_state(self, s, pos=True, vel=True, force=True):
+        n = self.n[s]
+        out = [np.empty((n, 3)) if f else None for f in (pos, vel, force)]
+        st = C.c_int64(0)
+        self._check(lib.dpd_batch_get_state(self.h, int(s), _ptr(out[0]), _ptr(out[1]),
+                                            _ptr(out[2]), C.byref(st)), "dpd_batch_get_state")
+        return out[0], out[1], out[2], st.value
+
+    def observables(self, s) -> dict:
+        o = dpd_obs()
+        self._check(lib.dpd_batch_observables(self.h, int(s), C.byref(o)),
+                    "dpd_batch_observables")
+        return o.as_dict()
+
+    def usage(self):
+        used = np.zeros(4, np.int64)
+        cap = np.zeros(4, np.int64)
+        ns = C.c_int32(0)
+        self._check(lib.dpd_batch_usage(self.h, _ptr(used), _ptr(cap), C.byref(ns)),
+                    "dpd_batch_usage")
+        return used, cap, ns.value
+
+    def sync(self):
+        self._check(lib.dpd_batch_sync(self.h), "dpd_batch_sync")
+
+    def launch_count(self) -> int:
+        return int(lib.dpd_batch_launch_count(self.h))
+
+    def close(self):
+        if self.h:
+            lib.dpd_batch_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
