@@ -14,6 +14,13 @@ synthetic, seeded.  Prints ONE JSON line (rank 0):
   fp64_plain  the plain FP64 path, one system per launch
   roofline    the pair kernel (dominant) against the ALU issue peak
   cpu_baseline  the FP64 oracle (cell-list mode) on the host cores
+  paper_tables  the shapes of the paper's Tables 1 and 3 (N = 5k..100k) on
+          the GPU, beside CAMUS's quoted CPU times (context)
+  alpha_helix   the paper's alpha-helix run, 10,000 steps
+  serving the batched half of the metric: a stream of independent systems
+          (box edge 8..24, two types, 10% of beads in chains) arriving as a
+          Poisson process, served by continuous batching; p50/p99 completion
+          latency and throughput, after the autotuner picked the launch shape
 
 --impl reference times the FP64 CPU oracle (the only reference: the paper
 publishes no code) on a bounded sample of the same workload.
@@ -167,6 +174,97 @@ def reference_arm(args):
     return 0
 
 
+# CAMUS's best ms/step on 2x Xeon E5-2640 (Table 1: fluid; Table 3: with the
+# 60-bead protein model), quoted as context.
+CAMUS_TABLE1_MS = {5000: 2.8, 10000: 5.1, 50000: 24.8, 100000: 48.7}
+CAMUS_TABLE3_MS = {5000: 2.8, 10000: 5.2, 50000: 25.9, 100000: 49.4}
+
+
+def paper_tables_leg(D, W, stream, steps=300, warmup=20):
+    """The paper's timing-table shapes on the GPU (FP32 and FP64)."""
+    import torch
+    out = []
+    for protein, ref in ((False, CAMUS_TABLE1_MS), (True, CAMUS_TABLE3_MS)):
+        for n, cpu_ms in ref.items():
+            w = W.camus_table(n, protein=protein)
+            row = {"table": 3 if protein else 1, "N": n, "camus_best_ms": cpu_ms}
+            for prec, tag in ((D.DPD_FP32, "f32"), (D.DPD_FP64, "f64")):
+                g = D.System.from_workload(w, precision=prec, cuda_stream=stream.cuda_stream)
+                g.set_state(w.pos, w.vel, 0)
+                g.step(warmup)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.step(steps)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1) / steps
+                g.close()
+                row["gpu_ms_" + tag] = ms
+            row["speedup_f32_vs_camus"] = cpu_ms / row["gpu_ms_f32"]
+            out.append(row)
+    return out
+
+
+def alpha_helix_leg(D, W, stream):
+    """The paper's alpha-helix run (10,000 steps, FP32) with its chain proxy."""
+    import torch
+    w = W.alpha_helix_24k()
+    g = D.System.from_workload(w, precision=D.DPD_FP32, cuda_stream=stream.cuda_stream)
+    g.set_state(w.pos, w.vel, 0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(w.steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    pos = g.get_state(vel=False, force=False)[0]
+    o = g.observables()
+    g.close()
+    p = pos[:60]
+    dist = {}
+    for k in (1, 2, 4):
+        d = p[k:] - p[:-k]
+        d -= w.L * np.round(d / w.L)
+        dist["d1%d" % (k + 1)] = float(np.linalg.norm(d, axis=1).mean())
+    return {"workload": "alpha_helix_24k: 24,000 beads, 20^3, 60-bead chain, Fig. 3b bonds, "
+                        "gamma=4.2, dt=0.02", "steps": w.steps, "ms_total": ms,
+            "ms_per_step": ms / w.steps, "final_chain_mean_distances": dist,
+            "kT": o["kT"], "p_total": o["p_total"]}
+
+
+def serving_leg(args, stream):
+    """Continuous batching of a Poisson stream of independent systems."""
+    from paper_1804_06205_gb300 import autotune, serving
+    from paper_1804_06205_gb300 import workloads as W
+    t0 = time.perf_counter()
+    table = autotune.tune(edges=(8.0, 12.0, 16.0, 20.0, 24.0), threads=(128, 256),
+                          beads=300_000, steps=8)
+    tune_s = time.perf_counter() - t0
+    reqs = W.serving_stream(nsys=args.serve_requests, rate_hz=args.serve_rate,
+                            steps=args.serve_steps)
+    srv = serving.Server(max_beads=3_000_000, max_cells=1_500_000, max_bonds=600_000,
+                         max_systems=160, chunk=args.serve_chunk, table=table,
+                         cuda_stream=stream.cuda_stream)
+    l0 = srv.batch.launch_count()
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    done = srv.run(reqs)
+    clocks = sampler.stop()
+    launches = srv.batch.launch_count() - l0
+    srv.close()
+    out = serving.summarize(done)
+    out.update({"rate_hz": args.serve_rate, "steps_per_request": args.serve_steps,
+                "chunk_steps": args.serve_chunk, "max_resident": srv.max_resident,
+                "chunks": srv.chunks, "gpu_launches": launches, "clocks": clocks,
+                "autotune": table, "autotune_s": tune_s,
+                "workload": "serving stream: %d systems, box edge U(8,24), rho=3, types A/B, "
+                            "a_AB U(25,50), 10%% of beads in harmonic 10-mers, dt=0.04; "
+                            "Poisson arrivals at %g/s; FP32" % (args.serve_requests,
+                                                                args.serve_rate),
+                "latency": "completion (final state on the host) - arrival"})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -180,6 +278,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--ref-box", type=int, default=40)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-steps", type=int, default=2000)
+    ap.add_argument("--serve-chunk", type=int, default=50)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -313,6 +417,13 @@ def main():
                "sample": "FP64 oracle, cell-list mode, full fluid_3m (N=3,000,000), 1 warm-up + "
                          "%d timed steps on all host cores" % args.cpu_steps}
 
+    serve = tables = helix = None
+    if ws == 1 and not args.no_serving:
+        serve = serving_leg(args, stream)
+    if ws == 1 and not args.no_extras:
+        tables = paper_tables_leg(D, W, stream)
+        helix = alpha_helix_leg(D, W, stream)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
@@ -324,7 +435,8 @@ def main():
                 "pair_interactions_per_s": ws * pairs * args.steps / (ms32 * 1e-3),
                 "phases_ms": dict(zip(("update_sort", "pair", "bond_vel"), phases)),
                 "fp64_plain": fp64, "roofline": roofline, "roofline_hbm_phases": other,
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+                "serving": serve, "paper_tables": tables, "alpha_helix": helix}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

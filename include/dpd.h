@@ -237,14 +237,15 @@ typedef struct {
 int dpd_batch_create(const dpd_batch_capacity *cap, const dpd_options *opt, dpd_batch **out);
 
 /* Add a system with its parameters (as dpd_create) and its state (as
- * dpd_set_state); *sys receives its index.  lambda and seed are per system.
- * Synchronises.  Errors: DPD_EINVAL, DPD_ENOMEM (does not fit: not admitted),
- * DPD_ECUDA. */
+ * dpd_set_state); *sys receives its index.  lambda, seed and tile_cells (the
+ * pair-kernel brick length, 0 = the batch's option or automatic) are per
+ * system.  Synchronises.  Errors: DPD_EINVAL, DPD_ENOMEM (does not fit: not
+ * admitted), DPD_ECUDA. */
 int dpd_batch_add(dpd_batch *b, const dpd_box *box, int64_t n, const int32_t *types,
                   int32_t ntypes, const double *a_ij, double gamma, double kT, double dt,
                   const dpd_bond *bonds, int64_t nbonds, const dpd_bond *morse, int64_t nmorse,
-                  double lambda, uint64_t seed, const double *pos, const double *vel,
-                  int64_t step, int32_t *sys);
+                  double lambda, uint64_t seed, int32_t tile_cells, const double *pos,
+                  const double *vel, int64_t step, int32_t *sys);
 
 /* Remove system sys and re-pack the others.  Synchronises. */
 int dpd_batch_remove(dpd_batch *b, int32_t sys);
@@ -263,6 +264,10 @@ int dpd_batch_usage(const dpd_batch *b, int64_t used[4], int64_t cap[4], int32_t
 
 int dpd_batch_sync(dpd_batch *b);
 int64_t dpd_batch_launch_count(const dpd_batch *b);
+
+/* Phase timing of the next batch steps, as dpd_profile_begin / _end. */
+int dpd_batch_profile_begin(dpd_batch *b, int64_t max_steps);
+int dpd_batch_profile_end(dpd_batch *b, double ms[3], int64_t *nsteps);
 const char *dpd_batch_last_error(const dpd_batch *b);
 int dpd_batch_destroy(dpd_batch *b);
 

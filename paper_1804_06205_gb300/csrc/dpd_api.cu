@@ -331,14 +331,15 @@ int dpd_batch_create(const dpd_batch_capacity *cap, const dpd_options *opt, dpd_
 int dpd_batch_add(dpd_batch *b, const dpd_box *box, int64_t n, const int32_t *types,
                   int32_t ntypes, const double *a_ij, double gamma, double kT, double dt,
                   const dpd_bond *bonds, int64_t nbonds, const dpd_bond *morse, int64_t nmorse,
-                  double lambda, uint64_t seed, const double *pos, const double *vel,
-                  int64_t step, int32_t *sys) {
+                  double lambda, uint64_t seed, int32_t tile_cells, const double *pos,
+                  const double *vel, int64_t step, int32_t *sys) {
     if (!b || !sys) return DPD_EINVAL;
     if (!pos || !vel) return fail(b->err, DPD_EINVAL, "pos or vel is NULL");
     dpd::Config c;
     const char *why = "";
     int rc = build_config(box, n, types, ntypes, a_ij, gamma, kT, dt, bonds, nbonds, morse,
-                          nmorse, lambda, seed, b->opt.noise, b->opt.tile_cells, c, &why);
+                          nmorse, lambda, seed, b->opt.noise,
+                          tile_cells > 0 ? tile_cells : b->opt.tile_cells, c, &why);
     if (rc) return fail(b->err, rc, why);
     int slot = -1;
     rc = b->eng->add_system(c, &slot);
@@ -393,6 +394,16 @@ int dpd_batch_sync(dpd_batch *b) {
 }
 
 int64_t dpd_batch_launch_count(const dpd_batch *b) { return b ? b->eng->launches() : 0; }
+
+int dpd_batch_profile_begin(dpd_batch *b, int64_t max_steps) {
+    if (!b || max_steps < 1 || max_steps > 100000) return DPD_EINVAL;
+    return b->eng->profile_begin(max_steps);
+}
+
+int dpd_batch_profile_end(dpd_batch *b, double ms[3], int64_t *nsteps) {
+    if (!b || !ms) return DPD_EINVAL;
+    return b->eng->profile_end(ms, nsteps);
+}
 
 const char *dpd_batch_last_error(const dpd_batch *b) {
     if (!b) return g_create_err.c_str();

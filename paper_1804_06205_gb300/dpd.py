@@ -35,7 +35,8 @@ EXPORTED = ("dpd_default_options", "dpd_create", "dpd_set_state", "dpd_step", "d
             "dpd_strerror", "dpd_last_error", "dpd_cells_noalloc", "dpd_batch_create",
             "dpd_batch_add", "dpd_batch_remove", "dpd_batch_step", "dpd_batch_get_state",
             "dpd_batch_observables", "dpd_batch_usage", "dpd_batch_sync", "dpd_batch_launch_count",
-            "dpd_batch_last_error", "dpd_batch_destroy")
+            "dpd_batch_last_error", "dpd_batch_destroy", "dpd_batch_profile_begin",
+            "dpd_batch_profile_end")
 
 
 class dpd_box(C.Structure):
@@ -108,7 +109,9 @@ def _load():
     lib.dpd_batch_create.argtypes = [P, P, P]
     lib.dpd_batch_add.argtypes = [P, P, C.c_int64, P, C.c_int32, P, C.c_double, C.c_double,
                                   C.c_double, P, C.c_int64, P, C.c_int64, C.c_double, C.c_uint64,
-                                  P, P, C.c_int64, P]
+                                  C.c_int32, P, P, C.c_int64, P]
+    lib.dpd_batch_profile_begin.argtypes = [P, C.c_int64]
+    lib.dpd_batch_profile_end.argtypes = [P, P, P]
     lib.dpd_batch_remove.argtypes = [P, C.c_int32]
     lib.dpd_batch_step.argtypes = [P, C.c_int64]
     lib.dpd_batch_get_state.argtypes = [P, C.c_int32, P, P, P, P]
@@ -304,7 +307,7 @@ class Batch:
             raise DPDError(rc, where, lib.dpd_batch_last_error(self.h).decode())
 
     def try_add(self, L, types, a, gamma, kT, dt, pos, vel, bonds=None, morse=None, lam=0.65,
-                seed=0, step=0):
+                seed=0, step=0, tile_cells=0):
         """Add a system with its state; returns its index, or None when it does
         not fit in the pools (DPD_ENOMEM: not admitted)."""
         L = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,))
@@ -321,16 +324,28 @@ class Batch:
         rc = lib.dpd_batch_add(self.h, C.byref(box), int(types.size), _ptr(types), ntypes,
                                _ptr(a), float(gamma), float(kT), float(dt), _ptr(brec), nb,
                                _ptr(mrec), nm, float(lam), int(seed) & 0xFFFFFFFFFFFFFFFF,
-                               _ptr(pos), _ptr(vel), int(step), C.byref(sys_))
+                               int(tile_cells), _ptr(pos), _ptr(vel), int(step), C.byref(sys_))
         if rc == DPD_ENOMEM:
             return None
         self._check(rc, "dpd_batch_add")
         self.n[sys_.value] = int(types.size)
         return sys_.value
 
-    def add_workload(self, w, step=0):
+    def add_workload(self, w, step=0, tile_cells=0):
         return self.try_add(w.L, w.types, w.a, w.gamma, w.kT, w.dt, w.pos, w.vel,
-                            bonds=w.bonds, lam=w.lam, seed=w.seed, step=step)
+                            bonds=w.bonds, lam=w.lam, seed=w.seed, step=step,
+                            tile_cells=tile_cells)
+
+    def profile_begin(self, max_steps):
+        self._check(lib.dpd_batch_profile_begin(self.h, int(max_steps)),
+                    "dpd_batch_profile_begin")
+
+    def profile_end(self):
+        ms = np.zeros(3)
+        n = C.c_int64(0)
+        self._check(lib.dpd_batch_profile_end(self.h, _ptr(ms), C.byref(n)),
+                    "dpd_batch_profile_end")
+        return ms, n.value
 
     def remove(self, s):
         self._check(lib.dpd_batch_remove(self.h, int(s)), "dpd_batch_remove")

@@ -132,6 +132,40 @@ def fluid_3m(seed=1004) -> Workload:
     return w
 
 
+def fluid_1m(seed=1004) -> Workload:
+    """The fluid_3m recipe in a 70^3 box (N = 1,029,000): state larger than
+    L2 at a third of the size, for kernel profiles."""
+    w = fluid(70.0, ntypes=2, a_same=25.0, a_cross=30.0, seed=seed, name="fluid_1m")
+    w.steps = 500
+    return w
+
+
+def camus_table(n: int, protein=False, seed=1007) -> Workload:
+    """The shapes of the paper's timing tables: a cubic box at rho = 3 holding
+    n beads with a_ij = 25 everywhere (Table 1); with protein=True the first
+    60 beads are the alpha-helix chain with its 1-2, 1-3 and 1-5 bonds and
+    the helix model's a_ij (Table 3)."""
+    edge = (n / 3.0) ** (1.0 / 3.0)
+    L = _box(edge)
+    rng = np.random.default_rng(seed + n)
+    pos = rng.uniform(0.0, 1.0, size=(n, 3)) * L
+    types = np.zeros(n, np.int32)
+    a = np.array([[25.0]])
+    bonds = empty_bonds()
+    gamma, dt = 4.5, 0.04
+    if protein:
+        beads = 60
+        pos[:beads] = random_walk_chains(rng, 1, beads, 0.6, L)
+        types = np.concatenate([np.zeros(beads, np.int32), np.ones(n - beads, np.int32)])
+        a = np.array([[50.0, 55.0], [55.0, 50.0]])
+        bonds = _helix_bonds(beads)
+        gamma, dt = 4.2, 0.02
+    pos = np.where(pos >= L, 0.0, pos)
+    vel = maxwell_velocities(rng, n)
+    return Workload("camus_%s_%d" % ("protein" if protein else "fluid", n), L, types, a, gamma,
+                    1.0, dt, 0.65, seed + n, pos, vel, bonds)
+
+
 def melt_98k(seed=1002, L=32.0, chain_len=10) -> Workload:
     L = _box(L)
     rng = np.random.default_rng(seed)
@@ -175,6 +209,19 @@ def peptide_192k(seed=1003, L=40.0, nchains=200, chain_len=20) -> Workload:
     return Workload("peptide_192k", L, types, a, 4.5, 1.0, 0.04, 0.65, seed, pos, vel, bonds)
 
 
+def _helix_bonds(beads: int) -> Dict[str, np.ndarray]:
+    """Fig. 3b's bond list for a skeletal chain of `beads` beads."""
+    i12 = np.arange(beads - 1)
+    i13 = np.arange(beads - 2)
+    i15 = np.arange(beads - 4)
+    return concat_bonds([
+        bond_records(i12, i12 + 1, KIND_HARMONIC, 0.6, 160.0),
+        bond_records(i13, i13 + 2, KIND_HARMONIC, 1.2, 80.0),
+        bond_records(i13, i13 + 2, KIND_MORSE_PAPER, 0.9, 12.0, 8.0),
+        bond_records(i15, i15 + 4, KIND_MORSE_PAPER, 0.6, 12.0, 8.0),
+    ])
+
+
 def alpha_helix_24k(seed=1006) -> Workload:
     """The paper's alpha-helix model: 24000 beads in a 20^3 box, one chain of 60
     skeletal beads (type 0) in water (type 1); a_SS=a_WW=50, a_SW=55;
@@ -189,15 +236,7 @@ def alpha_helix_24k(seed=1006) -> Workload:
     pos = np.concatenate([chain, water], axis=0)
     types = np.concatenate([np.zeros(beads, np.int32), np.ones(n - beads, np.int32)])
     a = np.array([[50.0, 55.0], [55.0, 50.0]])
-    i12 = np.arange(beads - 1)
-    i13 = np.arange(beads - 2)
-    i15 = np.arange(beads - 4)
-    bonds = concat_bonds([
-        bond_records(i12, i12 + 1, KIND_HARMONIC, 0.6, 160.0),
-        bond_records(i13, i13 + 2, KIND_HARMONIC, 1.2, 80.0),
-        bond_records(i13, i13 + 2, KIND_MORSE_PAPER, 0.9, 12.0, 8.0),
-        bond_records(i15, i15 + 4, KIND_MORSE_PAPER, 0.6, 12.0, 8.0),
-    ])
+    bonds = _helix_bonds(beads)
     vel = maxwell_velocities(rng, n)
     w = Workload("alpha_helix_24k", L, types, a, 4.2, 1.0, 0.02, 0.65, seed, pos, vel, bonds)
     w.steps = 10000
@@ -253,6 +292,7 @@ WORKLOADS = {
     "melt_98k": melt_98k,
     "peptide_192k": peptide_192k,
     "fluid_3m": fluid_3m,
+    "fluid_1m": fluid_1m,
     "alpha_helix_24k": alpha_helix_24k,
 }
 

@@ -1,0 +1,63 @@
+"""The continuous-batching server on the GPU: every request's final state
+equals its alone run bit for bit, whatever the systems it shared the batch
+with and the chunk boundaries, and requests that do not fit wait."""
+import numpy as np
+import pytest
+
+from paper_1804_06205_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def D():
+    from paper_1804_06205_gb300 import build
+    build.build()
+    from paper_1804_06205_gb300 import dpd
+    return dpd
+
+
+def mini_stream():
+    spec = [(0, 0.00, 23, 8.0), (1, 0.00, 17, 9.3), (2, 0.00, 31, 8.6), (3, 0.01, 9, 10.1),
+            (4, 0.05, 26, 8.2), (5, 0.30, 14, 9.0)]
+    return [W.Request(rid, t, steps, W.serving_system(40 + rid, edge=e, a_ab=30.0 + rid))
+            for rid, t, steps, e in spec]
+
+
+def alone(D, w, nsteps):
+    g = D.System.from_workload(w, precision=0)
+    g.set_state(w.pos, w.vel, 0)
+    g.step(nsteps)
+    out = g.get_state()
+    g.close()
+    return out
+
+
+@pytest.mark.parametrize("tight", [False, True])
+def test_served_results_equal_alone_runs(D, tight):
+    from paper_1804_06205_gb300 import serving
+    reqs = mini_stream()
+    if tight:   # room for about two systems: the rest wait for departures
+        nmax = max(r.workload.n for r in reqs)
+        srv = serving.Server(max_beads=2 * nmax + 100, max_cells=10 ** 5, max_bonds=10 ** 5,
+                             max_systems=8, chunk=7, keep_states=True)
+    else:
+        srv = serving.Server(max_beads=10 ** 6, max_cells=10 ** 6, max_bonds=10 ** 5,
+                             max_systems=16, chunk=7, keep_states=True)
+    done = srv.run(reqs)
+    srv.close()
+    assert sorted(d.rid for d in done) == list(range(len(reqs)))
+    first_done = min(d.done_s for d in done)
+    if tight:   # some request that arrived at once had to wait for a departure
+        assert srv.max_resident < len(reqs)
+        assert any(d.admit_s >= first_done for d in done if d.arrival_s < first_done)
+    else:   # the first three arrive together and are admitted together
+        assert srv.max_resident >= 3
+    for d in done:
+        r = reqs[d.rid]
+        ref = alone(D, r.workload, r.steps)
+        assert d.state[3] == r.steps
+        assert np.array_equal(d.state[0], ref[0]) and np.array_equal(d.state[1], ref[1])
+        assert d.admit_s >= d.arrival_s - 1e-9 and d.done_s > d.admit_s
+    s = serving.summarize(done)
+    assert s["requests"] == len(reqs) and s["p99_latency_s"] >= s["p50_latency_s"] > 0
