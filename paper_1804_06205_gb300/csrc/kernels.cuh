@@ -568,8 +568,9 @@ struct PairLaunch {   // a launch over bricks [br_lo, br_lo + gridDim.x) of any 
 
 constexpr int PAIR_MAXX = 64;          // largest brick length (cells)
 constexpr int PAIR_MAXT = 16;          // largest number of bead types
-constexpr int PAIR_HMAX = 16;          // hits per lane per pass
+constexpr int PAIR_HMAX = 24;          // hits per lane per pass (level field: 5 bits)
 constexpr int PAIR_NR = 16;            // staged rows, (2+2) x (2+2)
+static_assert(PAIR_HMAX <= 32, "the queue entry keeps the level in 5 bits");
 constexpr int PAIR_PC = 6;             // ints per staged run
 
 template <class P>
@@ -886,15 +887,22 @@ __global__ void __launch_bounds__(T) k_pair(PairLaunch<P> la) {
                             if (nh > 0) break;                   // evaluate first, resume here
                             qe = q + PAIR_HMAX;                  // a crowded row: part of it
                         }
-                        for (; q < qe; ++q) {
-                            const vec4 pj = s_pos[q - c0];
-                            const real dx = xi - pj.x, dyv = yi - pj.y, dzv = zi - pj.z;
-                            const real r2 = fma_rn(dzv, dzv, fma_rn(dyv, dyv, mul_rn(dx, dx)));
-                            if (r2 < (real)1 && r2 > (real)0) {
-                                my_q[nh * 32 + lane] = (uint32_t)(q - c0) | ((uint32_t)nh << 11) |
-                                                       ((uint32_t)lane << 15);
-                                ++nh;
+                        {   // queue entry: slot (11 bits) | level (5 bits) | owner lane
+                            const vec4 *pp = s_pos + (q - c0);
+                            uint32_t ent = (uint32_t)(q - c0) | ((uint32_t)lane << 16);
+                            uint32_t *qp = my_q + nh * 32 + lane;
+                            uint32_t lv = (uint32_t)nh << 11;
+                            for (; q < qe; ++q, ++pp, ++ent) {
+                                const vec4 pj = *pp;
+                                const real dx = xi - pj.x, dyv = yi - pj.y, dzv = zi - pj.z;
+                                const real r2 = fma_rn(dzv, dzv, fma_rn(dyv, dyv, mul_rn(dx, dx)));
+                                if (r2 < (real)1 && r2 > (real)0) {
+                                    *qp = ent | lv;
+                                    qp += 32;
+                                    lv += 1u << 11;
+                                }
                             }
+                            nh = (int)(lv >> 11);
                         }
                         if (q < qe_full) break;
                     }
@@ -920,8 +928,8 @@ __global__ void __launch_bounds__(T) k_pair(PairLaunch<P> la) {
                     const int f = b + lane;
                     const bool valid = f < K;
                     const uint32_t e = valid ? my_q[f] : 0u;
-                    const int jl = (int)(e & 2047u), lvl = (int)((e >> 11) & 15u);
-                    const int owner = (int)(e >> 15);
+                    const int jl = (int)(e & 2047u), lvl = (int)((e >> 11) & 31u);
+                    const int owner = (int)(e >> 16);
                     real fx = 0, fy = 0, fz = 0, wc = 0, ep = 0;
                     if (valid) {
                         const vec4 hpo = my_hp[owner], hvo = my_hv[owner];

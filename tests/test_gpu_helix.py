@@ -3,12 +3,17 @@ Figs. 3-5: 24,000 beads in a 20^3 box, a 60-bead skeletal chain with 1-2
 harmonic, 1-3 harmonic + modified Morse and 1-5 modified Morse bonds,
 gamma = 4.2, dt = 0.02) on the GPU against the oracle.
 
-Trajectories are chaotic, so the comparison is of averages over a run with
-block error bars: mean 1-2, 1-3 and 1-5 distances along the chain, kT and
-pressure.  The paper shows its result only as a picture (Fig. 5), so
-agreement with the paper itself is not pinned; the helicity proxy (mean 1-5
-distance, which the 1-5 Morse term pulls towards r_e = 0.6 and below, and
-the consistency of the sign of consecutive dihedral angles) is reported."""
+Two kinds of comparison:
+  * trajectories over a short horizon, while chaos has not yet amplified the
+    rounding differences (in the oracle, a 1e-12 displacement grows to ~4e-8
+    in 50 steps and to O(1) by step 150, the stiff chain leading);
+  * averages over 2,000 steps: kT and pressure with block error bars, and
+    the chain's mean 1-2, 1-3 and 1-5 distances within the spread that
+    oracle runs with different noise seeds show (a single 60-bead chain
+    samples few conformations in 2,000 steps: d15 ranged 0.50-0.58 over four
+    seeds).
+The paper shows its result only as a picture (Fig. 5), so agreement with
+the paper itself is not pinned."""
 import numpy as np
 import pytest
 
@@ -84,16 +89,38 @@ def mean_err(x, nblocks=5):
     return x.mean(), b.std(ddof=1) / np.sqrt(nblocks)
 
 
+@pytest.mark.parametrize("prec,nsteps,tol", [(1, 30, 1e-9), (0, 10, 1e-4)])
+def test_alpha_helix_short_trajectory_matches_oracle(D, prec, nsteps, tol):
+    import oracle as O
+    w = W.alpha_helix_24k()
+    s = O.System(w.L, w.types, w.a, w.gamma, w.kT, w.dt, w.lam, seed=w.seed, bonds=w.bonds)
+    st = O.State(s, w.pos, w.vel, 0, mode=O.MODE_CELLS)
+    st.run(nsteps)
+    g = D.System.from_workload(w, precision=prec)
+    g.set_state(w.pos, w.vel, 0)
+    g.step(nsteps)
+    pos, vel, _, step = g.get_state()
+    g.close()
+    assert step == nsteps
+    d = pos - st.pos
+    d -= w.L * np.round(d / w.L)
+    assert np.abs(d).max() < tol
+    assert np.abs(vel - st.vel).max() < 50 * tol
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_alpha_helix_statistics_match_oracle(D, oracle_series, prec):
     w = W.alpha_helix_24k()
     gpu = series_gpu(D, w, prec)
-    names = ("d12", "d13", "d15", "kT", "p")
-    floors = (0.01, 0.02, 0.03, 0.01, 0.15)
-    for k, (name, floor) in enumerate(zip(names, floors)):
+    # kT and p: bulk averages over 24,000 beads, block errors plus a floor
+    for k, name, floor in ((3, "kT", 0.005), (4, "p", 0.05)):
         mg, eg = mean_err(gpu[:, k])
         mo, eo = mean_err(oracle_series[:, k])
         tol = 4.0 * np.hypot(eg, eo) + floor
         assert abs(mg - mo) < tol, (name, mg, mo, tol)
+    # chain distances: within the seed-to-seed spread of the oracle
+    for k, name, spread in ((0, "d12", 0.04), (1, "d13", 0.10), (2, "d15", 0.12)):
+        mg, mo = mean_err(gpu[:, k])[0], mean_err(oracle_series[:, k])[0]
+        assert abs(mg - mo) < spread, (name, mg, mo)
     # the 1-5 Morse term has pulled the chain in from its random-walk start
     assert mean_err(gpu[:, 2])[0] < 0.7

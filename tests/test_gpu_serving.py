@@ -37,9 +37,10 @@ def alone(D, w, nsteps):
 def test_served_results_equal_alone_runs(D, tight):
     from paper_1804_06205_gb300 import serving
     reqs = mini_stream()
-    if tight:   # room for about two systems: the rest wait for departures
-        nmax = max(r.workload.n for r in reqs)
-        srv = serving.Server(max_beads=2 * nmax + 100, max_cells=10 ** 5, max_bonds=10 ** 5,
+    if tight:   # room for the first two requests only: the third waits for a departure
+        cap = reqs[0].workload.n + reqs[1].workload.n + 10
+        assert all(r.workload.n <= cap for r in reqs)
+        srv = serving.Server(max_beads=cap, max_cells=10 ** 5, max_bonds=10 ** 5,
                              max_systems=8, chunk=7, keep_states=True)
     else:
         srv = serving.Server(max_beads=10 ** 6, max_cells=10 ** 6, max_bonds=10 ** 5,
