@@ -489,6 +489,7 @@ class BatchEngine : public BatchBase {
         if (st & ST_TIMEOUT) status_host_ = DPD_ETIMEOUT;
         else if (st & ST_NONFINITE) status_host_ = DPD_EUNSTABLE;
         if (status_host_ == DPD_EUNSTABLE) err_ = "non-finite position, velocity or observable";
+        if (status_host_ == DPD_ETIMEOUT) err_ = "a bounded device wait gave up (pair-kernel staging)";
         return status_host_;
     }
 
@@ -697,6 +698,7 @@ class BatchEngine : public BatchBase {
         pl.ev = ev_;
         pl.atab = atab_;
         pl.counter = counter_;
+        pl.status = status_;
         switch (T_) {
             case 64:
                 return sample ? launch_pair_t<64, true>(pl, nbr) : launch_pair_t<64, false>(pl, nbr);

@@ -564,6 +564,7 @@ struct PairLaunch {   // a launch over bricks [br_lo, br_lo + gridDim.x) of any 
     vec4 *fpair, *ev;
     const real *atab;
     const long long *counter;
+    int *status;                        // sticky status bits (ST_TIMEOUT)
 };
 
 constexpr int PAIR_MAXX = 64;          // largest brick length (cells)
@@ -571,7 +572,7 @@ constexpr int PAIR_MAXT = 16;          // largest number of bead types
 constexpr int PAIR_HMAX = 24;          // hits per lane per pass (level field: 5 bits)
 constexpr int PAIR_NR = 16;            // staged rows, (2+2) x (2+2)
 static_assert(PAIR_HMAX <= 32, "the queue entry keeps the level in 5 bits");
-constexpr int PAIR_PC = 6;             // ints per staged run
+constexpr int PAIR_PC = 3;             // ints per staged run: source, slot, length
 
 template <class P>
 struct PairSmem {
@@ -592,6 +593,58 @@ struct PairSmem {
         return b;
     }
 };
+
+// Bulk asynchronous copies global -> shared (cp.async.bulk, completed on an
+// mbarrier as a byte count) and the mbarrier operations they need.  Addresses
+// and sizes must be multiples of 16 bytes.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *m, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// orders this thread's earlier generic-proxy shared accesses before later
+// async-proxy (bulk copy) accesses to the same memory
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *m, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *m) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(
+                     smem_u32(m))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *m, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(m)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: false if the phase has not completed after `tries` polls
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *m, uint32_t parity, int tries) {
+    for (int i = 0; i < tries; ++i)
+        if (mbar_try_wait(m, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *m) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(m))
+        : "memory");
+}
+constexpr int MBAR_TRIES = 1 << 22;
 
 // Philox4x32-10 with precomputed round keys (outputs 0 and 1).
 __device__ __forceinline__ uint2 philox_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
@@ -678,6 +731,12 @@ __global__ void __launch_bounds__(T) k_pair(PairLaunch<P> la) {
     uint32_t *s_q = reinterpret_cast<uint32_t *>(s_acce + NW * 32);
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    __shared__ __align__(8) uint64_t s_mbar;   // completion of the staging copies
+    if (tid == 0) {
+        mbar_init(&s_mbar, 1);
+        fence_mbar_init();
+    }
+    uint32_t mphase = 0;
     int bid = brick - D.brick0;
     const int bx = bid % a.nbx;
     bid /= a.nbx;
@@ -708,11 +767,11 @@ __global__ void __launch_bounds__(T) k_pair(PairLaunch<P> la) {
         if (lane == 0) {
             real sy, sz;
             if (P::kOffsets) {       // offset -> brick frame
-                sy = (real)uy * hy;
-                sz = (real)uz * hz;
+                sy = mul_rn((real)uy, hy);
+                sz = mul_rn((real)uz, hz);
             } else {                 // absolute -> brick frame, undoing the row's wrap
-                sy = (real)(uy - yy) * hy;
-                sz = (real)(uz - zz) * hz;
+                sy = mul_rn((real)(uy - yy), hy);
+                sz = mul_rn((real)(uz - zz), hz);
             }
             s_rsh[2 * r] = sy;
             s_rsh[2 * r + 1] = sz;
@@ -753,9 +812,6 @@ __global__ void __launch_bounds__(T) k_pair(PairLaunch<P> la) {
                 pc[0] = (int)a.cell_start[rowkey + xx];            // first source slot
                 pc[1] = s_cs[r * W + kfirst];                      // first staged slot
                 pc[2] = s_cs[r * W + k] - s_cs[r * W + kfirst];    // length
-                pc[3] = (int)(rowkey + xx);                        // key of its first cell
-                pc[4] = kfirst - 1;                                // ux of its first cell
-                pc[5] = xx;                                        // cx of its first cell
                 ++np;
                 kfirst = k;
             }
@@ -814,14 +870,16 @@ __global__ void __launch_bounds__(T) k_pair(PairLaunch<P> la) {
         if (active) {
             const uint32_t rowkey = ((uint32_t)(z0 + rz) * a.ny + (y0 + ry)) * a.nx;
             uxi = (int)(a.key[g] - rowkey) - x0;
+            // the same operations as the staging of this bead's own copy, so the
+            // two coincide bit for bit and the self pair has r^2 == 0 exactly
             if (P::kOffsets) {
-                hp.x = (real)uxi * hx + pr.x;
-                hp.y = (real)ry * hy + pr.y;
-                hp.z = (real)rz * hz + pr.z;
+                hp.x = fma_rn((real)uxi, hx, pr.x);
+                hp.y = add_rn(pr.y, mul_rn((real)ry, hy));
+                hp.z = add_rn(pr.z, mul_rn((real)rz, hz));
             } else {
-                hp.x = pr.x - (real)x0 * hx;
-                hp.y = pr.y - (real)y0 * hy;
-                hp.z = pr.z - (real)z0 * hz;
+                hp.x = add_rn(pr.x, mul_rn((real)(-x0), hx));
+                hp.y = add_rn(pr.y, mul_rn((real)(-y0), hy));
+                hp.z = add_rn(pr.z, mul_rn((real)(-z0), hz));
             }
         }
         my_hp[lane] = hp;
@@ -837,26 +895,51 @@ __global__ void __launch_bounds__(T) k_pair(PairLaunch<P> la) {
         for (int c0 = 0; c0 < S; c0 += cap) {
             const int c1 = min(S, c0 + cap);
             if (staged_lo != c0) {
-                __syncthreads();   // everyone is done with the previous chunk
-                for (int pcn = wid; pcn < NRe * 3; pcn += NW) {
-                    const int *pc = s_pc + pcn * PAIR_PC;
+                fence_proxy_async_smem();   // this chunk's reads before the next copies
+                __syncthreads();            // everyone is done with the previous chunk
+                if (tid < NRe * 3) {        // one thread per source run: positions, v~
+                    const int *pc = s_pc + tid * PAIR_PC;
                     const int src = pc[0], dst = pc[1], len = pc[2];
                     const int lo = max(dst, c0), hi = min(dst + len, c1);
+                    if (lo < hi) {
+                        const uint32_t bytes = (uint32_t)(hi - lo) * (uint32_t)sizeof(vec4);
+                        mbar_expect_tx(&s_mbar, 2u * bytes);
+                        bulk_g2s(s_pos + (lo - c0), a.pos + src + (lo - dst), bytes, &s_mbar);
+                        bulk_g2s(s_vt + (lo - c0), a.vt + src + (lo - dst), bytes, &s_mbar);
+                    }
+                }
+                __syncthreads();
+                if (tid == 0) mbar_arrive(&s_mbar);
+                const bool got = mbar_wait_bounded(&s_mbar, mphase, MBAR_TRIES);
+                mphase ^= 1u;
+                if (__syncthreads_or(!got)) {   // a copy never completed: flag it, leave
+                    if (tid == 0) atomicOr(la.status, ST_TIMEOUT);
+                    mbar_wait_bounded(&s_mbar, mphase ^ 1u, MBAR_TRIES);
+                    return;
+                }
+                // into the brick's frame, cell by cell: x by the cell's place in
+                // the brick, y and z by the row's shift
+                for (int e = tid; e < NRe * W; e += T) {
+                    const int r = e / W, k = e - r * W;
+                    if (k > Xe + 1) continue;                 // the row-end entry
+                    const int lo = max(s_cs[e], c0), hi = min(s_cs[e + 1], c1);
                     if (lo >= hi) continue;
-                    const int r = pcn / 3;
-                    const uint32_t k0 = (uint32_t)pc[3];
-                    const int ux0 = pc[4];
-                    const real shx = (real)(ux0 - pc[5]) * hx;
+                    real sx;
+                    if (P::kOffsets) {
+                        sx = (real)(k - 1);
+                    } else {   // absolute x -> brick frame, undoing the cell's wrap
+                        int cx = x0 + k - 1;
+                        cx += cx < 0 ? a.nx : (cx >= a.nx ? -a.nx : 0);
+                        sx = mul_rn((real)(k - 1 - cx), hx);
+                    }
                     const real sy = s_rsh[2 * r], sz = s_rsh[2 * r + 1];
-                    for (int q = lo + lane; q < hi; q += 32) {
-                        const int gq = src + (q - dst);
-                        vec4 p = a.pos[gq];
-                        if (P::kOffsets) p.x = (real)((int)(a.key[gq] - k0) + ux0) * hx + p.x;
-                        else p.x = p.x + shx;
-                        p.y += sy;
-                        p.z += sz;
+                    for (int q = lo; q < hi; ++q) {
+                        vec4 p = s_pos[q - c0];
+                        if (P::kOffsets) p.x = fma_rn(sx, hx, p.x);
+                        else p.x = add_rn(p.x, sx);
+                        p.y = add_rn(p.y, sy);
+                        p.z = add_rn(p.z, sz);
                         s_pos[q - c0] = p;
-                        s_vt[q - c0] = a.vt[gq];
                     }
                 }
                 staged_lo = c0;
