@@ -524,7 +524,7 @@ class BatchEngine : public BatchBase {
         // staged capacity: the mean of (BY+2)(BZ+2)(X+2) cells plus ~4 sigma;
         // larger neighbourhoods are staged in chunks (slots must fit 11 bits)
         const double mean = (h.BY + 2) * (h.BZ + 2) * (h.X + 2) * per_cell;
-        int cap = (int)std::ceil(mean + 4.0 * std::sqrt(mean) + 32.0);
+        int cap = (int)std::ceil(mean + 3.0 * std::sqrt(mean) + 16.0);
         cap = (cap + 31) / 32 * 32;
         const int cap_max = (int)((96 * 1024) / (2 * sizeof(vec4)));
         h.cap = std::max(64, std::min(cap, std::min(cap_max, 2016)));
@@ -639,15 +639,17 @@ class BatchEngine : public BatchBase {
 
     // shared memory of the pair kernel: the largest brick among live systems
     int update_smem() {
-        int capmax = 64, xmax = 1;
+        int capmax = 64, xmax = 1, ntmax = 1;
         for (int s : order_) {
             capmax = std::max(capmax, hs_[s].cap);
             xmax = std::max(xmax, hs_[s].X);
+            ntmax = std::max(ntmax, (int)hs_[s].cfg.ntypes);
         }
-        if (capmax != capmax_ || xmax != xmax_) drop_graphs();
+        if (capmax != capmax_ || xmax != xmax_ || ntmax != ntmax_) drop_graphs();
         capmax_ = capmax;
         xmax_ = xmax;
-        smem_ = PairSmem<P>::bytes(capmax_, xmax_, T_);
+        ntmax_ = ntmax;
+        smem_ = PairSmem<P>::bytes(capmax_, xmax_, T_, ntmax_);
         int rc;
         switch (T_) {
             case 64:
@@ -690,6 +692,7 @@ class BatchEngine : public BatchBase {
         pl.br_lo = br_lo;
         pl.capmax = capmax_;
         pl.Xmax = xmax_;
+        pl.ntmax = ntmax_;
         pl.pos = pos_;
         pl.vt = vt_;
         pl.key = key_;
@@ -942,7 +945,7 @@ class BatchEngine : public BatchBase {
     std::vector<int> order_;               // live systems in pool order
     int used_beads_ = 0, used_cells_ = 0, used_bricks_ = 0, used_bonds_ = 0;
     int nred_all_ = 0, nrsys_all_ = 0;
-    int capmax_ = 0, xmax_ = 0;
+    int capmax_ = 0, xmax_ = 0, ntmax_ = 1;
     size_t smem_ = 0;
     vec4 *pos_ = nullptr, *pos_tmp_ = nullptr, *vel_[2] = {nullptr, nullptr},
          *frc_[2] = {nullptr, nullptr}, *vt_ = nullptr, *fpair_ = nullptr, *ev_ = nullptr;

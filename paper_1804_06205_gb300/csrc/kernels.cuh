@@ -565,31 +565,32 @@ struct PairLaunch {   // a launch over bricks [br_lo, br_lo + gridDim.x) of any 
     const real *atab;
     const long long *counter;
     int *status;                        // sticky status bits (ST_TIMEOUT)
+    int ntmax;                          // largest number of bead types (a_ij table size)
 };
 
 constexpr int PAIR_MAXX = 64;          // largest brick length (cells)
 constexpr int PAIR_MAXT = 16;          // largest number of bead types
 constexpr int PAIR_HMAX = 24;          // hits per lane per pass (level field: 5 bits)
 constexpr int PAIR_NR = 16;            // staged rows, (2+2) x (2+2)
-static_assert(PAIR_HMAX <= 32, "the queue entry keeps the level in 5 bits");
+static_assert(PAIR_HMAX < 32, "a lane per level holds the compacted level starts");
 constexpr int PAIR_PC = 3;             // ints per staged run: source, slot, length
 
 template <class P>
 struct PairSmem {
     static __host__ __device__ size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
-    static size_t bytes(int cap, int X, int T) {
+    static size_t bytes(int cap, int X, int T, int ntmax) {
         using real = typename P::real;
         using vec4 = typename P::vec4;
         size_t b = 2 * (size_t)cap * sizeof(vec4);                 // staged positions, v~
-        b += PAIR_NR * (size_t)(X + 3) * sizeof(int);              // staged cell starts
+        b += 2 * PAIR_NR * (size_t)(X + 3) * sizeof(int);          // staged / source cell starts
         b += PAIR_NR * 3 * PAIR_PC * sizeof(int) + 4 * 4 * sizeof(int);   // runs, home rows
         b = align16(b);
-        b += PAIR_MAXT * PAIR_MAXT * sizeof(real) + PAIR_NR * 2 * sizeof(real);
+        b += (size_t)ntmax * ntmax * sizeof(real) + PAIR_NR * 2 * sizeof(real);
         b = align16(b);
         const size_t nw = (size_t)T / 32;
         b += nw * 32 * 2 * sizeof(vec4);                           // home beads (pos, v~)
         b += nw * 32 * sizeof(vec4) + nw * 32 * sizeof(real);      // owners' sums
-        b += nw * PAIR_HMAX * 32 * sizeof(uint32_t);               // hit queue
+        b += nw * PAIR_HMAX * 32 * sizeof(uint16_t);               // hit queue
         return b;
     }
 };
@@ -718,17 +719,18 @@ __global__ void __launch_bounds__(T) k_pair(PairLaunch<P> la) {
     vec4 *s_pos = reinterpret_cast<vec4 *>(smem);
     vec4 *s_vt = s_pos + cap;
     int *s_cs = reinterpret_cast<int *>(s_vt + cap);
-    int *s_pc = s_cs + PAIR_NR * (la.Xmax + 3);
+    int *s_src = s_cs + PAIR_NR * (la.Xmax + 3);
+    int *s_pc = s_src + PAIR_NR * (la.Xmax + 3);
     int *s_hr = s_pc + PAIR_NR * 3 * PAIR_PC;        // home rows: staged row, first, count, global
     size_t off = PairSmem<P>::align16((size_t)((unsigned char *)(s_hr + 16) - smem));
     real *s_a = reinterpret_cast<real *>(smem + off);
-    real *s_rsh = s_a + PAIR_MAXT * PAIR_MAXT;       // per staged row: y, z frame shift
+    real *s_rsh = s_a + la.ntmax * la.ntmax;         // per staged row: y, z frame shift
     off = PairSmem<P>::align16((size_t)((unsigned char *)(s_rsh + 2 * PAIR_NR) - smem));
     vec4 *s_hp = reinterpret_cast<vec4 *>(smem + off);
     vec4 *s_hv = s_hp + NW * 32;
     vec4 *s_acc = s_hv + NW * 32;
     real *s_acce = reinterpret_cast<real *>(s_acc + NW * 32);
-    uint32_t *s_q = reinterpret_cast<uint32_t *>(s_acce + NW * 32);
+    uint16_t *s_q = reinterpret_cast<uint16_t *>(s_acce + NW * 32);
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     __shared__ __align__(8) uint64_t s_mbar;   // completion of the staging copies
@@ -756,13 +758,15 @@ __global__ void __launch_bounds__(T) k_pair(PairLaunch<P> la) {
         zz += zz < 0 ? a.nz : (zz >= a.nz ? -a.nz : 0);
         const uint32_t rowkey = ((uint32_t)zz * a.ny + yy) * a.nx;
         for (int k = lane; k < W; k += 32) {
-            int cnt = 0;
+            int cnt = 0, first = 0;
             if (k <= Xe + 1) {
                 int xx = x0 + k - 1;
                 xx += xx < 0 ? a.nx : (xx >= a.nx ? -a.nx : 0);
-                cnt = (int)(a.cell_start[rowkey + xx + 1] - a.cell_start[rowkey + xx]);
+                first = (int)a.cell_start[rowkey + xx];
+                cnt = (int)a.cell_start[rowkey + xx + 1] - first;
             }
             s_cs[r * W + k] = cnt;
+            s_src[r * W + k] = first;
         }
         if (lane == 0) {
             real sy, sz;
@@ -806,10 +810,8 @@ __global__ void __launch_bounds__(T) k_pair(PairLaunch<P> la) {
             int xk = x0 + k - 1;
             xk += xk >= a.nx ? -a.nx : 0;
             if (k == Xe + 2 || xk == 0) {
-                int xx = x0 + kfirst - 1;
-                xx += xx < 0 ? a.nx : (xx >= a.nx ? -a.nx : 0);
                 int *pc = s_pc + (r * 3 + np) * PAIR_PC;
-                pc[0] = (int)a.cell_start[rowkey + xx];            // first source slot
+                pc[0] = s_src[r * W + kfirst];                     // first source slot
                 pc[1] = s_cs[r * W + kfirst];                      // first staged slot
                 pc[2] = s_cs[r * W + k] - s_cs[r * W + kfirst];    // length
                 ++np;
@@ -823,9 +825,8 @@ __global__ void __launch_bounds__(T) k_pair(PairLaunch<P> la) {
         int hcount = 0, first = 0, gfirst = 0, sr = 0;
         if (ry < BYe && rz < BZe) {
             sr = (ry + 1) + SY * (rz + 1);
-            const uint32_t rowkey = ((uint32_t)(z0 + rz) * a.ny + (y0 + ry)) * a.nx;
-            gfirst = (int)a.cell_start[rowkey + x0];
-            hcount = (int)(a.cell_start[rowkey + x0 + Xe] - a.cell_start[rowkey + x0]);
+            gfirst = s_src[sr * W + 1];
+            hcount = s_cs[sr * W + Xe + 1] - s_cs[sr * W + 1];
         }
         s_hr[4 * tid] = sr;
         s_hr[4 * tid + 1] = first;
@@ -850,7 +851,7 @@ __global__ void __launch_bounds__(T) k_pair(PairLaunch<P> la) {
     const int nt = a.ntypes;
     vec4 *my_hp = s_hp + wid * 32, *my_hv = s_hv + wid * 32, *my_acc = s_acc + wid * 32;
     real *my_acce = s_acce + wid * 32;
-    uint32_t *my_q = s_q + wid * PAIR_HMAX * 32;
+    uint16_t *my_q = s_q + wid * PAIR_HMAX * 32;
     const unsigned lt_mask = (1u << lane) - 1u;
     int staged_lo = -1;
 
@@ -970,49 +971,49 @@ __global__ void __launch_bounds__(T) k_pair(PairLaunch<P> la) {
                             if (nh > 0) break;                   // evaluate first, resume here
                             qe = q + PAIR_HMAX;                  // a crowded row: part of it
                         }
-                        {   // queue entry: slot (11 bits) | level (5 bits) | owner lane
+                        {   // queue [level][lane]: the staged slot of each hit
                             const vec4 *pp = s_pos + (q - c0);
-                            uint32_t ent = (uint32_t)(q - c0) | ((uint32_t)lane << 16);
-                            uint32_t *qp = my_q + nh * 32 + lane;
-                            uint32_t lv = (uint32_t)nh << 11;
+                            uint16_t ent = (uint16_t)(q - c0);
+                            uint16_t *qp = my_q + nh * 32 + lane;
                             for (; q < qe; ++q, ++pp, ++ent) {
                                 const vec4 pj = *pp;
                                 const real dx = xi - pj.x, dyv = yi - pj.y, dzv = zi - pj.z;
                                 const real r2 = fma_rn(dzv, dzv, fma_rn(dyv, dyv, mul_rn(dx, dx)));
                                 if (r2 < (real)1 && r2 > (real)0) {
-                                    *qp = ent | lv;
+                                    *qp = ent;
                                     qp += 32;
-                                    lv += 1u << 11;
                                 }
                             }
-                            nh = (int)(lv >> 11);
+                            nh = (int)((qp - my_q) >> 5);
                         }
                         if (q < qe_full) break;
                     }
                     more = r9 < 9;
                 }
                 __syncwarp();
-                // ---- compact level by level: all first hits, then all second hits, ...
-                int K = 0;
+                // ---- compact level by level: all first hits, then all second hits,
+                // ...; entries gain the owner lane (slot | owner << 11) and lane m
+                // keeps the start K_m of level m (lane nlev: the total)
+                int K = 0, nlev = 0, myK = 0;
                 for (int m = 0; m < PAIR_HMAX; ++m) {
                     const unsigned A = __ballot_sync(FULL, nh > m);
                     if (A == 0u) break;
-                    if (A != FULL || K != 32 * m) {
-                        uint32_t e = 0;
-                        if (nh > m) e = my_q[m * 32 + lane];
-                        __syncwarp();
-                        if (nh > m) my_q[K + __popc(A & lt_mask)] = e;
-                        __syncwarp();
-                    }
+                    if (lane == m) myK = K;
+                    uint32_t e = 0;
+                    if (nh > m) e = my_q[m * 32 + lane];
+                    __syncwarp();
+                    if (nh > m) my_q[K + __popc(A & lt_mask)] = (uint16_t)(e | ((uint32_t)lane << 11));
+                    __syncwarp();
                     K += __popc(A);
+                    nlev = m + 1;
                 }
+                if (lane == nlev) myK = K;
                 // ---- evaluate 32 hits at a time, sums updated level by level
                 for (int b = 0; b < K; b += 32) {
                     const int f = b + lane;
                     const bool valid = f < K;
-                    const uint32_t e = valid ? my_q[f] : 0u;
-                    const int jl = (int)(e & 2047u), lvl = (int)((e >> 11) & 31u);
-                    const int owner = (int)(e >> 16);
+                    const uint32_t e = valid ? (uint32_t)my_q[f] : 0u;
+                    const int jl = (int)(e & 2047u), owner = (int)(e >> 11);
                     real fx = 0, fy = 0, fz = 0, wc = 0, ep = 0;
                     if (valid) {
                         const vec4 hpo = my_hp[owner], hvo = my_hv[owner];
@@ -1041,10 +1042,14 @@ __global__ void __launch_bounds__(T) k_pair(PairLaunch<P> la) {
                             ep = (real)0.5 * fc * w;
                         }
                     }
-                    const int lv_lo = __shfl_sync(FULL, lvl, 0);
-                    const int lv_hi = __shfl_sync(FULL, lvl, min(31, K - 1 - b));
+                    // the levels this batch spans; a lane's level is the one whose
+                    // range [K_lv, K_lv+1) holds its entry
+                    const int last = min(b + 31, K - 1);
+                    const int lv_lo = __popc(__ballot_sync(FULL, lane <= nlev && myK <= b)) - 1;
+                    const int lv_hi = __popc(__ballot_sync(FULL, lane <= nlev && myK <= last)) - 1;
                     for (int lv = lv_lo; lv <= lv_hi; ++lv) {
-                        if (valid && lvl == lv) {
+                        const int klo = __shfl_sync(FULL, myK, lv), khi = __shfl_sync(FULL, myK, lv + 1);
+                        if (valid && f >= klo && f < khi) {
                             vec4 s = my_acc[owner];
                             s.x = add_rn(s.x, fx);
                             s.y = add_rn(s.y, fy);
