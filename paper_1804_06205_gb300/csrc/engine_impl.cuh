@@ -524,10 +524,10 @@ class BatchEngine : public BatchBase {
         // staged capacity: the mean of (BY+2)(BZ+2)(X+2) cells plus ~4 sigma;
         // larger neighbourhoods are staged in chunks (slots must fit 11 bits)
         const double mean = (h.BY + 2) * (h.BZ + 2) * (h.X + 2) * per_cell;
-        int cap = (int)std::ceil(mean + 3.0 * std::sqrt(mean) + 16.0);
-        cap = (cap + 31) / 32 * 32;
+        int cap = (int)std::ceil(mean + 3.0 * std::sqrt(mean) + 8.0);
+        cap = (cap + 15) / 16 * 16;
         const int cap_max = (int)((96 * 1024) / (2 * sizeof(vec4)));
-        h.cap = std::max(64, std::min(cap, std::min(cap_max, 2016)));
+        h.cap = std::max(T_ + 64, std::min(cap, std::min(cap_max, 2016)));
     }
 
     // Descriptor, bead -> system and brick -> system maps, a_ij table and
@@ -649,7 +649,8 @@ class BatchEngine : public BatchBase {
         capmax_ = capmax;
         xmax_ = xmax;
         ntmax_ = ntmax;
-        smem_ = PairSmem<P>::bytes(capmax_, xmax_, T_, ntmax_);
+        smem_ = PairSmem<P>::bytes(capmax_, xmax_, T_, ntmax_, true);
+        smem_n_ = PairSmem<P>::bytes(capmax_, xmax_, T_, ntmax_, false);
         int rc;
         switch (T_) {
             case 64:
@@ -667,18 +668,19 @@ class BatchEngine : public BatchBase {
     // (the attribute is per kernel, shared by all handles: only ever raised)
     template <int T, bool S>
     int set_pair_smem_t() {
-        if (smem_ <= 48 * 1024) return DPD_OK;
+        const size_t need = S ? smem_ : smem_n_;
+        if (need <= 48 * 1024) return DPD_OK;
         cudaFuncAttributes fa;
         DPD_CU(cudaFuncGetAttributes(&fa, k_pair<P, T, S>));
-        if ((size_t)fa.maxDynamicSharedSizeBytes >= smem_) return DPD_OK;
+        if ((size_t)fa.maxDynamicSharedSizeBytes >= need) return DPD_OK;
         DPD_CU(cudaFuncSetAttribute(k_pair<P, T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem_));
+                                    (int)need));
         return DPD_OK;
     }
 
     template <int T, bool S>
     int launch_pair_t(const PairLaunch<P> &pl, int nbr) {
-        k_pair<P, T, S><<<nbr, T, smem_, stream_>>>(pl);
+        k_pair<P, T, S><<<nbr, T, S ? smem_ : smem_n_, stream_>>>(pl);
         ++launches_;
         DPD_CU(cudaGetLastError());
         return DPD_OK;
@@ -946,7 +948,7 @@ class BatchEngine : public BatchBase {
     int used_beads_ = 0, used_cells_ = 0, used_bricks_ = 0, used_bonds_ = 0;
     int nred_all_ = 0, nrsys_all_ = 0;
     int capmax_ = 0, xmax_ = 0, ntmax_ = 1;
-    size_t smem_ = 0;
+    size_t smem_ = 0, smem_n_ = 0;   // pair-kernel shared memory: sampled, plain
     vec4 *pos_ = nullptr, *pos_tmp_ = nullptr, *vel_[2] = {nullptr, nullptr},
          *frc_[2] = {nullptr, nullptr}, *vt_ = nullptr, *fpair_ = nullptr, *ev_ = nullptr;
     uint32_t *key_ = nullptr, *key_tmp_ = nullptr, *rank_ = nullptr, *src_ = nullptr;

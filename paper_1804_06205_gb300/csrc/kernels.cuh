@@ -573,12 +573,13 @@ constexpr int PAIR_MAXT = 16;          // largest number of bead types
 constexpr int PAIR_HMAX = 24;          // hits per lane per pass (level field: 5 bits)
 constexpr int PAIR_NR = 16;            // staged rows, (2+2) x (2+2)
 static_assert(PAIR_HMAX < 32, "a lane per level holds the compacted level starts");
+constexpr int PAIR_THREADS_PER_SM = 896; // FP32 register budget: 28 warps per SM
 constexpr int PAIR_PC = 3;             // ints per staged run: source, slot, length
 
 template <class P>
 struct PairSmem {
     static __host__ __device__ size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
-    static size_t bytes(int cap, int X, int T, int ntmax) {
+    static size_t bytes(int cap, int X, int T, int ntmax, bool sample) {
         using real = typename P::real;
         using vec4 = typename P::vec4;
         size_t b = 2 * (size_t)cap * sizeof(vec4);                 // staged positions, v~
@@ -588,9 +589,10 @@ struct PairSmem {
         b += (size_t)ntmax * ntmax * sizeof(real) + PAIR_NR * 2 * sizeof(real);
         b = align16(b);
         const size_t nw = (size_t)T / 32;
-        b += nw * 32 * 2 * sizeof(vec4);                           // home beads (pos, v~)
-        b += nw * 32 * sizeof(vec4) + nw * 32 * sizeof(real);      // owners' sums
+        b += nw * 32 * sizeof(vec4);                               // owners' sums
+        if (sample) b += nw * 32 * sizeof(real);                   // owners' energies
         b += nw * PAIR_HMAX * 32 * sizeof(uint16_t);               // hit queue
+        b += nw * 32 * sizeof(uint16_t);                           // owners' staged slots
         return b;
     }
 };
@@ -676,7 +678,7 @@ __device__ __forceinline__ double theta_pair(uint2 x, int noise, double) {
 }
 
 template <class P, int T, bool SAMPLE>
-__global__ void __launch_bounds__(T) k_pair(PairLaunch<P> la) {
+__global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) k_pair(PairLaunch<P> la) {
     using real = typename P::real;
     using vec4 = typename P::vec4;
     constexpr int NW = T / 32;
@@ -726,11 +728,10 @@ __global__ void __launch_bounds__(T) k_pair(PairLaunch<P> la) {
     real *s_a = reinterpret_cast<real *>(smem + off);
     real *s_rsh = s_a + la.ntmax * la.ntmax;         // per staged row: y, z frame shift
     off = PairSmem<P>::align16((size_t)((unsigned char *)(s_rsh + 2 * PAIR_NR) - smem));
-    vec4 *s_hp = reinterpret_cast<vec4 *>(smem + off);
-    vec4 *s_hv = s_hp + NW * 32;
-    vec4 *s_acc = s_hv + NW * 32;
-    real *s_acce = reinterpret_cast<real *>(s_acc + NW * 32);
-    uint16_t *s_q = reinterpret_cast<uint16_t *>(s_acce + NW * 32);
+    vec4 *s_acc = reinterpret_cast<vec4 *>(smem + off);
+    real *s_acce = reinterpret_cast<real *>(s_acc + NW * 32);   // SAMPLE only
+    uint16_t *s_q = reinterpret_cast<uint16_t *>(s_acce + (SAMPLE ? NW * 32 : 0));
+    uint16_t *s_own = s_q + NW * PAIR_HMAX * 32;   // each owner's staged slot
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     __shared__ __align__(8) uint64_t s_mbar;   // completion of the staging copies
@@ -849,9 +850,16 @@ __global__ void __launch_bounds__(T) k_pair(PairLaunch<P> la) {
     const uint32_t s_lo = (uint32_t)(unsigned long long)sctr;
     const uint32_t s_hi = (uint32_t)((unsigned long long)sctr >> 32);
     const int nt = a.ntypes;
-    vec4 *my_hp = s_hp + wid * 32, *my_hv = s_hv + wid * 32, *my_acc = s_acc + wid * 32;
+    vec4 *my_acc = s_acc + wid * 32;
     real *my_acce = s_acce + wid * 32;
     uint16_t *my_q = s_q + wid * PAIR_HMAX * 32;
+    uint16_t *my_own = s_own + wid * 32;
+    // The whole neighbourhood usually fits one chunk: owners are then read
+    // from their own staged copies.  Otherwise chunks are staged into the
+    // first cap - 32 NW slots and each warp keeps copies of its owners in the
+    // last 32 NW.
+    const bool one_chunk = S <= cap;
+    const int capc = one_chunk ? cap : cap - 32 * NW;
     const unsigned lt_mask = (1u << lane) - 1u;
     int staged_lo = -1;
 
@@ -883,18 +891,24 @@ __global__ void __launch_bounds__(T) k_pair(PairLaunch<P> la) {
                 hp.z = add_rn(pr.z, mul_rn((real)(-z0), hz));
             }
         }
-        my_hp[lane] = hp;
-        my_hv[lane] = a.vt[g];
+        if (one_chunk) {
+            my_own[lane] = (uint16_t)(active ? s_cs[sr_home * W + 1] + (hb - s_hr[4 * hr + 1]) : 0);
+        } else {
+            const int qo = capc + wid * 32 + lane;
+            s_pos[qo] = hp;
+            s_vt[qo] = a.vt[g];
+            my_own[lane] = (uint16_t)qo;
+        }
         my_acc[lane] = mk4<vec4, real>((real)0, (real)0, (real)0, (real)0);
-        my_acce[lane] = (real)0;
+        if (SAMPLE) my_acce[lane] = (real)0;
         // distances from the bead to the faces of its cell (pruning)
         const real lxd = hp.x - (real)uxi * hx, uxd = hx - lxd;
         const real lyd = hp.y - (real)ry * hy, uyd = hy - lyd;
         const real lzd = hp.z - (real)rz * hz, uzd = hz - lzd;
         const real cut2 = (real)1.0001;
 
-        for (int c0 = 0; c0 < S; c0 += cap) {
-            const int c1 = min(S, c0 + cap);
+        for (int c0 = 0; c0 < S; c0 += capc) {
+            const int c1 = min(S, c0 + capc);
             if (staged_lo != c0) {
                 fence_proxy_async_smem();   // this chunk's reads before the next copies
                 __syncthreads();            // everyone is done with the previous chunk
@@ -1016,7 +1030,8 @@ __global__ void __launch_bounds__(T) k_pair(PairLaunch<P> la) {
                     const int jl = (int)(e & 2047u), owner = (int)(e >> 11);
                     real fx = 0, fy = 0, fz = 0, wc = 0, ep = 0;
                     if (valid) {
-                        const vec4 hpo = my_hp[owner], hvo = my_hv[owner];
+                        const int qo = my_own[owner];
+                        const vec4 hpo = s_pos[qo], hvo = s_vt[qo];
                         const vec4 pj = s_pos[jl], vj = s_vt[jl];
                         const real dx = hpo.x - pj.x, dyv = hpo.y - pj.y, dzv = hpo.z - pj.z;
                         const real r2 = fma_rn(dzv, dzv, fma_rn(dyv, dyv, mul_rn(dx, dx)));
