@@ -989,7 +989,22 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
                             const vec4 *pp = s_pos + (q - c0);
                             uint16_t ent = (uint16_t)(q - c0);
                             uint16_t *qp = my_q + nh * 32 + lane;
-                            for (; q < qe; ++q, ++pp, ++ent) {
+                            for (; q + 1 < qe; q += 2, pp += 2, ent += 2) {   // two at a time
+                                const vec4 pa = pp[0], pb = pp[1];
+                                const real ax = xi - pa.x, ay = yi - pa.y, az = zi - pa.z;
+                                const real bx = xi - pb.x, by = yi - pb.y, bz = zi - pb.z;
+                                const real ra = fma_rn(az, az, fma_rn(ay, ay, mul_rn(ax, ax)));
+                                const real rb = fma_rn(bz, bz, fma_rn(by, by, mul_rn(bx, bx)));
+                                if (ra < (real)1 && ra > (real)0) {
+                                    *qp = ent;
+                                    qp += 32;
+                                }
+                                if (rb < (real)1 && rb > (real)0) {
+                                    *qp = (uint16_t)(ent + 1);
+                                    qp += 32;
+                                }
+                            }
+                            if (q < qe) {
                                 const vec4 pj = *pp;
                                 const real dx = xi - pj.x, dyv = yi - pj.y, dzv = zi - pj.z;
                                 const real r2 = fma_rn(dzv, dzv, fma_rn(dyv, dyv, mul_rn(dx, dx)));
@@ -997,6 +1012,7 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
                                     *qp = ent;
                                     qp += 32;
                                 }
+                                ++q;
                             }
                             nh = (int)((qp - my_q) >> 5);
                         }
