@@ -59,6 +59,11 @@ PAIR_OPS_PER_BEAD = 40.5 * 7 + 6.28 * 103
 # the index arrays (~24 B): 172 B; bonds+velocity read f_pair/vel/frc/id
 # (52 B) and write vel/frc (32 B): 84 B.
 SORT_BYTES_PER_BEAD = 172.0
+# DRAM bytes (read + written) per bead of one k_pair launch, from an ncu
+# capture of the current pair kernel on the 70^3 fluid (dram__bytes_read.sum +
+# dram__bytes_write.sum = 39.45 MB for 1,029,000 beads); the launch's force
+# writes stay in L2 and reach DRAM in later kernels.
+PAIR_DRAM_BYTES_PER_BEAD = 38.34
 BOND_BYTES_PER_BEAD = 84.0
 
 
@@ -398,7 +403,8 @@ def main():
     achieved = PAIR_OPS_PER_BEAD * w.n / (pair_ms * 1e-3)
     roofline = {"bound": "alu", "kernel": "k_pair", "achieved": achieved / 1e12,
                 "peak": alu_peak / 1e12, "unit": "Tops/s", "frac": achieved / alu_peak,
-                "traffic": None,
+                "traffic": PAIR_DRAM_BYTES_PER_BEAD * w.n,
+                "traffic_note": "bytes per launch, ncu dram read+write scaled by bead count",
                 "ops_per_bead": PAIR_OPS_PER_BEAD, "launch_ms": pair_ms,
                 "peak_source": "152 SMs x 128 lanes x %.0f MHz (one op per lane per cycle)"
                                % peaks["sm_max_mhz"]}
