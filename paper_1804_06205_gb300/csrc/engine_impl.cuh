@@ -719,8 +719,8 @@ class BatchEngine : public BatchBase {
     int enqueue_sort(int b_lo, int b_hi, int c_lo, int c_hi, int old, int nxt) {
         const int C = c_hi - c_lo, nb = (C + SCAN_B - 1) / SCAN_B;
         k_scan1<<<nb, SCAN_T, 0, stream_>>>(count_ + c_lo, C, bsum_);
-        k_scan2b<<<1, SCAN_T, 0, stream_>>>(bsum_, nb, cell_start_ + c_lo, C, (uint32_t)b_lo);
-        k_scan3<<<nb, SCAN_T, 0, stream_>>>(count_ + c_lo, C, bsum_, cell_start_ + c_lo);
+        k_scan3b<<<nb, SCAN_T, 0, stream_>>>(count_ + c_lo, C, bsum_, cell_start_ + c_lo,
+                                             (uint32_t)b_lo);
         ScatterArgs<P> sa;
         sa.b_lo = b_lo;
         sa.b_hi = b_hi;
@@ -733,13 +733,13 @@ class BatchEngine : public BatchBase {
         sa.src = src_;
         sa.sid = sid_;
         k_scatter<P><<<blocks(b_hi - b_lo), 256, 0, stream_>>>(sa);
-        k_cellfix<<<blocks(C), 256, 0, stream_>>>(c_lo, c_hi, cell_start_, src_, sid_);
         GatherArgs<P> ga;
         ga.b_lo = b_lo;
         ga.b_hi = b_hi;
         ga.sys = sys_;
         ga.bsys = bsys_;
         ga.src = src_;
+        ga.cell_start = cell_start_;
         ga.sid = sid_;
         ga.pos_tmp = pos_tmp_;
         ga.vel_old = vel_[old];
@@ -751,9 +751,9 @@ class BatchEngine : public BatchBase {
         ga.vt = vt_;
         ga.key = key_;
         ga.id = id_[nxt];
-        ga.inv_perm = inv_perm_;
+        ga.inv_perm = used_bonds_ > 0 ? inv_perm_ : nullptr;
         k_gather<P><<<blocks(b_hi - b_lo), 256, 0, stream_>>>(ga);
-        launches_ += 6;
+        launches_ += 4;
         DPD_CU(cudaGetLastError());
         return DPD_OK;
     }

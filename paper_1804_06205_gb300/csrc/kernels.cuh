@@ -15,8 +15,8 @@
 //                 cell occupancy histogram (atomics on counts)
 //   k_scan*       3.    exclusive scan of the counts -> cell_start
 //   k_scatter     3.    slot = cell_start[key] + arrival rank
-//   k_cellfix     3.    canonical (cell, id) order inside each cell
-//   k_gather      3.    permute the state into the new order, v~ = v + lambda dt f
+//   k_gather      3.    canonical (cell, id) order: each arrival ranks itself among
+//                       its cell's ids and moves its state there; v~ = v + lambda dt f
 //   k_pair        4.    eq. 3-4 + dissipative/random pair terms, 27-cell full shell
 //   k_bond_vel    4.-5. eqs. 6-8 bonded terms, then v += dt/2 (f + f')
 //   k_reduce*           FP64 sums for the observables (sampled steps only)
@@ -391,44 +391,38 @@ static __global__ void __launch_bounds__(SCAN_T) k_scan2(uint32_t *bsum, int nb,
     if (threadIdx.x == 0) cell_start[ncell] = carry;
 }
 
-static __global__ void __launch_bounds__(SCAN_T) k_scan3(uint32_t *count, int ncell,
-                                                  const uint32_t *bsum, uint32_t *cell_start) {
-    const int base = blockIdx.x * SCAN_B + threadIdx.x * SCAN_V;
-    uint32_t v[SCAN_V];
-    uint32_t s = 0;
-#pragma unroll
-    for (int k = 0; k < SCAN_V; ++k) {
-        v[k] = (base + k < ncell) ? count[base + k] : 0u;
-        s += v[k];
-    }
-    __shared__ uint32_t tot;
-    uint32_t run = block_excl_scan(s, &tot) + bsum[blockIdx.x];
-#pragma unroll
-    for (int k = 0; k < SCAN_V; ++k)
-        if (base + k < ncell) {
-            cell_start[base + k] = run;
-            run += v[k];
-            count[base + k] = 0u;
-        }
-}
 
-// The same scans with the starts offset by `base` (the first bead slot of the
-// cell range being sorted).
-static __global__ void __launch_bounds__(SCAN_T) k_scan2b(uint32_t *bsum, int nb,
-                                                   uint32_t *cell_start, int ncell,
+// Second pass of the two-pass scan: each block adds up the sums of the blocks
+// before it (a few hundred values) instead of waiting for a separate scan of
+// the block sums; cell starts are offset by `base`, and the last block writes
+// the end of the range.  The counts are cleared for the next step.
+static __global__ void __launch_bounds__(SCAN_T) k_scan3b(uint32_t *count, int ncell,
+                                                   const uint32_t *bsum, uint32_t *cell_start,
                                                    uint32_t base) {
     __shared__ uint32_t tot;
-    uint32_t carry = base;
-    for (int b0 = 0; b0 < nb; b0 += SCAN_T) {
-        const int b = b0 + threadIdx.x;
-        const uint32_t v = b < nb ? bsum[b] : 0u;
-        const uint32_t ex = block_excl_scan(v, &tot);
-        if (b < nb) bsum[b] = carry + ex;
-        carry += tot;
-        __syncthreads();
+    uint32_t before = 0;
+    for (int j = threadIdx.x; j < (int)blockIdx.x; j += SCAN_T) before += bsum[j];
+    block_excl_scan(before, &tot);
+    before = tot;
+    const int b0 = blockIdx.x * SCAN_B + threadIdx.x * SCAN_V;
+    uint32_t v[SCAN_V];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_V; ++k) {
+        v[k] = (b0 + k < ncell) ? count[b0 + k] : 0u;
+        sum += v[k];
     }
-    if (threadIdx.x == 0) cell_start[ncell] = carry;
+    uint32_t run = block_excl_scan(sum, &tot) + before + base;
+#pragma unroll
+    for (int k = 0; k < SCAN_V; ++k)
+        if (b0 + k < ncell) {
+            cell_start[b0 + k] = run;
+            run += v[k];
+            count[b0 + k] = 0u;
+        }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == SCAN_T - 1) cell_start[ncell] = run;
 }
+
 
 template <class P>
 struct ScatterArgs {
@@ -451,43 +445,24 @@ __global__ void __launch_bounds__(256) k_scatter(ScatterArgs<P> a) {
     a.sid[slot] = a.id_old[t];
 }
 
-// Atomic ranks give an arbitrary order inside a cell; sort each cell's
-// entries by bead id (cells hold ~3 beads: insertion sort).
-static __global__ void __launch_bounds__(256) k_cellfix(int c_lo, int c_hi,
-                                                 const uint32_t *cell_start, uint32_t *src,
-                                                 int32_t *sid) {
-    const int c = c_lo + blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= c_hi) return;
-    const int b = (int)cell_start[c], e = (int)cell_start[c + 1];
-    for (int i = b + 1; i < e; ++i) {
-        const int32_t ki = sid[i];
-        const uint32_t si = src[i];
-        int j = i - 1;
-        while (j >= b && sid[j] > ki) {
-            sid[j + 1] = sid[j];
-            src[j + 1] = src[j];
-            --j;
-        }
-        sid[j + 1] = ki;
-        src[j + 1] = si;
-    }
-}
-
 template <class P>
 struct GatherArgs {
     using vec4 = typename P::vec4;
     int b_lo, b_hi;
     const SysDesc<P> *sys;
     const int *bsys;
-    const uint32_t *src;
+    const uint32_t *src, *cell_start;
     const int32_t *sid;
     const vec4 *pos_tmp, *vel_old, *frc_old;
     const uint32_t *key_tmp;
     vec4 *pos, *vel, *frc, *vt;
     uint32_t *key;
-    int32_t *id, *inv_perm;
+    int32_t *id, *inv_perm;          // inv_perm: null when no system has bonds
 };
 
+// Atomic ranks put the beads of a cell in arrival order.  Each arrival finds
+// its canonical place, the cell's start plus the number of the cell's beads
+// with a smaller id (cells hold ~3 beads), and moves its state there.
 template <class P>
 __global__ void __launch_bounds__(256) k_gather(GatherArgs<P> a) {
     const int t = a.b_lo + blockIdx.x * blockDim.x + threadIdx.x;
@@ -495,16 +470,21 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs<P> a) {
     const SysDesc<P> &D = a.sys[a.bsys[t]];
     const uint32_t s = a.src[t];
     const int32_t i = a.sid[t];
+    const uint32_t k = a.key_tmp[s];
+    const uint32_t c = (uint32_t)D.cell0 + k;
+    const int b = (int)a.cell_start[c], e = (int)a.cell_start[c + 1];
+    int u = b;
+    for (int q = b; q < e; ++q) u += a.sid[q] < i;
     const typename P::vec4 v = a.vel_old[s], f = a.frc_old[s];
     const typename P::real lam_dt = D.lam_dt;
-    a.pos[t] = a.pos_tmp[s];
-    a.key[t] = a.key_tmp[s];
-    a.vel[t] = v;
-    a.frc[t] = f;
-    a.id[t] = i;
-    a.inv_perm[D.bead0 + i] = t;
+    a.pos[u] = a.pos_tmp[s];
+    a.key[u] = k;
+    a.vel[u] = v;
+    a.frc[u] = f;
+    a.id[u] = i;
+    if (a.inv_perm) a.inv_perm[D.bead0 + i] = u;
     // Fig. 1 step 2: velocity predictor used by the dissipative force
-    a.vt[t] = mk4<typename P::vec4, typename P::real>(v.x + lam_dt * f.x, v.y + lam_dt * f.y,
+    a.vt[u] = mk4<typename P::vec4, typename P::real>(v.x + lam_dt * f.x, v.y + lam_dt * f.y,
                                                       v.z + lam_dt * f.z, P::pack_id(i));
 }
 
