@@ -53,18 +53,21 @@ WORKLOAD_DESC = ("fluid_3m: periodic 100^3 box, rho=3, N=3,000,000, types A/B 50
 # (r, w, e, v_ij.e: 13; Philox4x32-10: 60; two uniforms: 6; Box-Muller: 6;
 # scalar force: 8; vector force: 3; add to both beads: 6; id order: 2).
 PAIR_OPS_PER_BEAD = 40.5 * 7 + 6.28 * 103
-# Minimum HBM bytes of the other phases (per bead per step, FP32 path):
-# update+sort reads pos/key/vel/frc (52 B) and writes pos/key/rank (24 B),
-# then the gather moves pos/key/vel/frc/id (56 B) and writes v~ (16 B) plus
-# the index arrays (~24 B): 172 B; bonds+velocity read f_pair/vel/frc/id
-# (52 B) and write vel/frc (32 B): 84 B.
+# Minimum HBM bytes of the other phases (per bead per step, FP32 path).
+# Sort (scans, scatter, gather): the scans ~4 B; the scatter reads system,
+# key, rank and id (16 B) plus the cell start and writes source and id (8 B);
+# the gather reads source, id, key and cell bounds (~16 B) and the moving
+# state pos/vel/frc (48 B), then writes pos/key/vel/frc/id/v~ (72 B): 172 B.
+# Bonds + velocity, which also make the next step's position update: read
+# f_pair/vel/frc/pos/key/id/system (68 B), write vel/frc/pos'/key'/rank and
+# the cell count (60 B), plus the bond table pointers: ~144 B.
 SORT_BYTES_PER_BEAD = 172.0
 # DRAM bytes (read + written) per bead of one k_pair launch, from an ncu
 # capture of the current pair kernel on the 70^3 fluid (dram__bytes_read.sum +
 # dram__bytes_write.sum = 39.45 MB for 1,029,000 beads); the launch's force
 # writes stay in L2 and reach DRAM in later kernels.
 PAIR_DRAM_BYTES_PER_BEAD = 38.34
-BOND_BYTES_PER_BEAD = 84.0
+BOND_BYTES_PER_BEAD = 144.0
 
 
 def _peaks():

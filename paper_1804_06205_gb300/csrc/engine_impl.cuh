@@ -275,14 +275,19 @@ class BatchEngine : public BatchBase {
             if (!hs_[k].has_state) return DPD_ENOSTATE;
         int rc = peek_status();
         if (rc) return rc;
+        // A plain step is never the last of a call: its bond kernel also does the
+        // next step's position update, which that step then skips.
+        bool updated = false;
         for (int64_t k = 0; k < nsteps; ++k) {
             // running means: one system's steps decide when (a batch of one)
             const bool acc = bc_.sample_every > 0 && order_.size() == 1 &&
                              ((hs_[order_[0]].step + 1) % bc_.sample_every) == 0;
             const bool sample = acc || (k == nsteps - 1);
-            const int variant = acc ? 2 : (sample ? 1 : 0);
-            rc = bc_.use_graph ? launch_graph(variant) : enqueue_step(sample, acc, false);
+            const int variant = (acc ? 2 : (sample ? 1 : 0)) + (updated ? 3 : 0);
+            rc = bc_.use_graph ? launch_graph(variant)
+                               : enqueue_step(sample, acc, false, !updated, !sample);
             if (rc) return rc;
+            updated = !sample;
             for (int s : order_) hs_[s].step += 1;
         }
         return DPD_OK;
@@ -759,7 +764,7 @@ class BatchEngine : public BatchBase {
     }
 
     // bonds (+ velocity update unless init) over beads [b_lo, b_hi)
-    int enqueue_bonds(bool init, bool sample, int b_lo, int b_hi) {
+    int enqueue_bonds(bool init, bool sample, int b_lo, int b_hi, bool fuse = false) {
         BondArgs<P> ba;
         ba.b_lo = b_lo;
         ba.b_hi = b_hi;
@@ -776,10 +781,18 @@ class BatchEngine : public BatchBase {
         ba.vel = vel_[cur_];
         ba.frc = frc_[cur_];
         ba.ev = ev_;
+        ba.pos_tmp = pos_tmp_;
+        ba.key_tmp = key_tmp_;
+        ba.rank = rank_;
+        ba.count = count_;
+        ba.counter = counter_;
+        ba.status = status_;
         const int g = blocks(b_hi - b_lo);
         if (init) {
             if (sample) k_bond_vel<P, true, true><<<g, 256, 0, stream_>>>(ba);
             else k_bond_vel<P, true, false><<<g, 256, 0, stream_>>>(ba);
+        } else if (fuse) {
+            k_bond_vel<P, false, false, true><<<g, 256, 0, stream_>>>(ba);
         } else {
             if (sample) k_bond_vel<P, false, true><<<g, 256, 0, stream_>>>(ba);
             else k_bond_vel<P, false, false><<<g, 256, 0, stream_>>>(ba);
@@ -800,7 +813,10 @@ class BatchEngine : public BatchBase {
         return DPD_OK;
     }
 
-    int enqueue_step(bool sample, bool accumulate, bool capturing) {
+    // One step of every resident system.  with_update: run the position update
+    // here (else the previous step's bond kernel did it); fuse: this step's bond
+    // kernel does the next step's update (never on a sampled step).
+    int enqueue_step(bool sample, bool accumulate, bool capturing, bool with_update, bool fuse) {
         int rc = mark(0, capturing);
         if (rc) return rc;
         UpdArgs<P> ua;
@@ -818,14 +834,17 @@ class BatchEngine : public BatchBase {
         ua.count = count_;
         ua.counter = counter_;
         ua.status = status_;
-        k_update<P><<<blocks(used_beads_), 256, 0, stream_>>>(ua);
-        ++launches_;
-        DPD_CU(cudaGetLastError());
+        if (with_update) {
+            k_update<P><<<blocks(used_beads_), 256, 0, stream_>>>(ua);
+            ++launches_;
+            DPD_CU(cudaGetLastError());
+        }
         const int nxt = cur_ ^ 1;
         if ((rc = enqueue_sort(0, used_beads_, 0, used_cells_, cur_, nxt))) return rc;
         cur_ = nxt;
         if ((rc = mark(1, capturing)) || (rc = launch_pair(sample, 0, used_bricks_)) ||
-            (rc = mark(2, capturing)) || (rc = enqueue_bonds(false, sample, 0, used_beads_)))
+            (rc = mark(2, capturing)) ||
+            (rc = enqueue_bonds(false, sample, 0, used_beads_, fuse && !sample)))
             return rc;
         if (sample && (rc = enqueue_reduce(0, nred_all_, 0, nrsys_all_, accumulate))) return rc;
         return mark(3, capturing);
@@ -890,7 +909,8 @@ class BatchEngine : public BatchBase {
             const int64_t l0 = launches_;
             cudaGraph_t graph = nullptr;
             DPD_CU(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal));
-            int rc = enqueue_step(variant >= 1, variant == 2, true);
+            const int base = variant % 3;
+            int rc = enqueue_step(base >= 1, base == 2, true, variant < 3, base == 0);
             cudaError_t e = cudaStreamEndCapture(stream_, &graph);
             cur_ = cur0;   // capture did not execute anything
             if (rc) {
@@ -968,7 +988,7 @@ class BatchEngine : public BatchBase {
     int cur_ = 0;
     int64_t launches_ = 0;
     int status_host_ = 0;
-    GraphSlot graphs_[2][3];
+    GraphSlot graphs_[2][6];   // [parity][variant]: plain/sampled/accumulating x with/without update
     cudaEvent_t ph_[4] = {nullptr, nullptr, nullptr, nullptr};
     std::vector<cudaEvent_t> prof_ev_;
     int64_t prof_max_ = 0, prof_n_ = 0;

@@ -242,6 +242,40 @@ __device__ __forceinline__ int move_cell(float &o, float h, float inv_h, int c, 
     return cc < 0 ? cc + n : cc;
 }
 
+// Fig. 1 steps 1-2 for one bead: r += dt v + dt^2/2 f, wrapped, and its new
+// cell.  Shared by k_update and by the bond/velocity kernel, which does it for
+// the next step while v and f are still in registers, so both give the same
+// bits.
+template <class P>
+__device__ __forceinline__ void update_bead(const SysDesc<P> &D, const typename P::vec4 &p,
+                                            uint32_t key_in, const typename P::vec4 &v,
+                                            const typename P::vec4 &f, typename P::vec4 &out,
+                                            uint32_t &key, int *status) {
+    using real = typename P::real;
+    const real dt = D.dt, hdt2 = D.half_dt2;
+    const real ddx = fma_rn(hdt2, f.x, mul_rn(dt, v.x));
+    const real ddy = fma_rn(hdt2, f.y, mul_rn(dt, v.y));
+    const real ddz = fma_rn(hdt2, f.z, mul_rn(dt, v.z));
+    if (P::kOffsets) {
+        int cx, cy, cz;
+        decode_key3(key_in, D.nx, D.ny, cx, cy, cz);
+        float ox = add_rn((float)p.x, (float)ddx), oy = add_rn((float)p.y, (float)ddy),
+              oz = add_rn((float)p.z, (float)ddz);
+        if (!(isfinite(ox) && isfinite(oy) && isfinite(oz))) {
+            atomicOr(status, ST_NONFINITE);
+            ox = oy = oz = 0.0f;
+        }
+        cx = move_cell(ox, D.hf[0], D.inv_hf[0], cx, D.nx);
+        cy = move_cell(oy, D.hf[1], D.inv_hf[1], cy, D.ny);
+        cz = move_cell(oz, D.hf[2], D.inv_hf[2], cz, D.nz);
+        key = ((uint32_t)cz * (uint32_t)D.ny + (uint32_t)cy) * (uint32_t)D.nx + (uint32_t)cx;
+        out = mk4<typename P::vec4, real>((real)ox, (real)oy, (real)oz, p.w);
+    } else {
+        place_bead<P>(D, add_rn((double)p.x, (double)ddx), add_rn((double)p.y, (double)ddy),
+                      add_rn((double)p.z, (double)ddz), p.w, out, key, status, ST_NONFINITE);
+    }
+}
+
 template <class P>
 struct UpdArgs {
     using vec4 = typename P::vec4;
@@ -258,36 +292,14 @@ struct UpdArgs {
 
 template <class P>
 __global__ void __launch_bounds__(256) k_update(UpdArgs<P> a) {
-    using real = typename P::real;
     const int t = a.b_lo + blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= a.b_hi) return;
     const int s = a.bsys[t];
     const SysDesc<P> &D = a.sys[s];
     if (t == D.bead0) a.counter[s] += 1;   // evaluation counter of this step's force
-    const typename P::vec4 p = a.pos[t], v = a.vel[t], f = a.frc[t];
-    const real dt = D.dt, hdt2 = D.half_dt2;
-    const real ddx = dt * v.x + hdt2 * f.x;
-    const real ddy = dt * v.y + hdt2 * f.y;
-    const real ddz = dt * v.z + hdt2 * f.z;
     typename P::vec4 out;
     uint32_t key;
-    if (P::kOffsets) {
-        int cx, cy, cz;
-        decode_key3(a.key[t], D.nx, D.ny, cx, cy, cz);
-        float ox = (float)p.x + (float)ddx, oy = (float)p.y + (float)ddy, oz = (float)p.z + (float)ddz;
-        if (!(isfinite(ox) && isfinite(oy) && isfinite(oz))) {
-            atomicOr(a.status, ST_NONFINITE);
-            ox = oy = oz = 0.0f;
-        }
-        cx = move_cell(ox, D.hf[0], D.inv_hf[0], cx, D.nx);
-        cy = move_cell(oy, D.hf[1], D.inv_hf[1], cy, D.ny);
-        cz = move_cell(oz, D.hf[2], D.inv_hf[2], cz, D.nz);
-        key = ((uint32_t)cz * (uint32_t)D.ny + (uint32_t)cy) * (uint32_t)D.nx + (uint32_t)cx;
-        out = mk4<typename P::vec4, real>((real)ox, (real)oy, (real)oz, p.w);
-    } else {
-        place_bead<P>(D, (double)p.x + (double)ddx, (double)p.y + (double)ddy,
-                      (double)p.z + (double)ddz, p.w, out, key, a.status, ST_NONFINITE);
-    }
+    update_bead<P>(D, a.pos[t], a.key[t], a.vel[t], a.frc[t], out, key, a.status);
     a.pos_tmp[t] = out;
     a.key_tmp[t] = key;
     a.rank[t] = atomicAdd(&a.count[D.cell0 + key], 1u);
@@ -1132,6 +1144,11 @@ struct BondArgs {
     const int32_t *bpartner;   // partner's local id
     const vec4 *bpar;      // r0, k, alpha, kind
     vec4 *vel, *frc, *ev;
+    // the next step's update (FUSE): as UpdArgs
+    vec4 *pos_tmp;
+    uint32_t *key_tmp, *rank, *count;
+    long long *counter;
+    int *status;
 };
 
 template <class P>
@@ -1161,13 +1178,15 @@ __device__ __forceinline__ void bond_disp(const BondArgs<P> &a, const SysDesc<P>
     }
 }
 
-template <class P, bool INIT, bool SAMPLE>
+template <class P, bool INIT, bool SAMPLE, bool FUSE = false>
 __global__ void __launch_bounds__(256) k_bond_vel(BondArgs<P> a) {
+    static_assert(!FUSE || !INIT, "the fused update follows a velocity update");
     using real = typename P::real;
     using vec4 = typename P::vec4;
     const int t = a.b_lo + blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= a.b_hi) return;
-    const SysDesc<P> &D = a.sys[a.bsys[t]];
+    const int sysi = a.bsys[t];
+    const SysDesc<P> &D = a.sys[sysi];
     const vec4 fp = a.fpair[t];
     real fx = fp.x, fy = fp.y, fz = fp.z, wb = 0, eb = 0;
     const int32_t i = a.id[t];
@@ -1186,13 +1205,25 @@ __global__ void __launch_bounds__(256) k_bond_vel(BondArgs<P> a) {
             eb += U;
         }
     }
+    vec4 vn;
     if (!INIT) {
         const real hdt = D.half_dt;
         const vec4 v = a.vel[t], f = a.frc[t];
-        a.vel[t] = mk4<vec4, real>(v.x + hdt * (f.x + fx), v.y + hdt * (f.y + fy),
-                                   v.z + hdt * (f.z + fz), (real)0);
+        vn = mk4<vec4, real>(v.x + hdt * (f.x + fx), v.y + hdt * (f.y + fy),
+                             v.z + hdt * (f.z + fz), (real)0);
+        a.vel[t] = vn;
     }
-    a.frc[t] = mk4<vec4, real>(fx, fy, fz, (real)0);
+    const vec4 fn = mk4<vec4, real>(fx, fy, fz, (real)0);
+    a.frc[t] = fn;
+    if (FUSE) {   // Fig. 1 steps 1-2 of the next step, from this step's v and f
+        if (t == D.bead0) a.counter[sysi] += 1;
+        vec4 out;
+        uint32_t key;
+        update_bead<P>(D, a.pos[t], a.key[t], vn, fn, out, key, a.status);
+        a.pos_tmp[t] = out;
+        a.key_tmp[t] = key;
+        a.rank[t] = atomicAdd(&a.count[D.cell0 + key], 1u);
+    }
     if (SAMPLE) {
         const vec4 e = a.ev[t];
         a.ev[t] = mk4<vec4, real>(e.x, e.y, wb, eb);
