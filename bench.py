@@ -146,6 +146,25 @@ def _dist():
     return ws, rank, local
 
 
+def reduce_over_ranks(x, op, dist=None, device="cpu"):
+    """x reduced over the ranks of the default process group (op "max" or
+    "sum"); x itself on a single process."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def replica_throughput(units_local, secs_local, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas: the units all ranks
+    processed divided by the slowest rank's time."""
+    units = reduce_over_ranks(units_local, "sum", dist, device)
+    secs = reduce_over_ranks(secs_local, "max", dist, device)
+    return units / secs, secs
+
+
 def run_cpu_oracle(w, warmup, steps):
     """The FP64 oracle's cell-list mode on all host cores."""
     import oracle as O
@@ -311,11 +330,7 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_over_ranks(x, "max", dist, "cuda")
 
     from paper_1804_06205_gb300 import build as B
     if rank == 0:
@@ -362,8 +377,8 @@ def main():
     sampler = ClockSampler(local)
     ms32, launches, clocks, phases, pairs = timed(D.DPD_FP32, args.warmup, args.steps,
                                                   sampler=sampler)
-    ms32 = max_over_ranks(ms32)
-    value = ws * w.n * args.steps / (ms32 * 1e-3)
+    value, secs32 = replica_throughput(w.n * args.steps, ms32 * 1e-3, dist, "cuda")
+    ms32 = secs32 * 1e3
 
     # ---- plain FP64 path
     fp64 = None
