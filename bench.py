@@ -67,6 +67,10 @@ SORT_BYTES_PER_BEAD = 172.0
 # dram__bytes_write.sum = 39.45 MB for 1,029,000 beads); the launch's force
 # writes stay in L2 and reach DRAM in later kernels.
 PAIR_DRAM_BYTES_PER_BEAD = 38.34
+# Thread instructions executed per bead by one k_pair launch, from the same
+# capture (smsp__inst_executed.sum x thread_inst_executed_per_inst_executed):
+# the issued work, against which the issue-rate roofline is taken.
+PAIR_THREAD_INST_PER_BEAD = 6376.0
 BOND_BYTES_PER_BEAD = 144.0
 
 
@@ -424,6 +428,11 @@ def main():
                 "traffic": PAIR_DRAM_BYTES_PER_BEAD * w.n,
                 "traffic_note": "bytes per launch, ncu dram read+write scaled by bead count",
                 "ops_per_bead": PAIR_OPS_PER_BEAD, "launch_ms": pair_ms,
+                "issued": {"thread_inst_per_bead": PAIR_THREAD_INST_PER_BEAD,
+                           "achieved": PAIR_THREAD_INST_PER_BEAD * w.n / (pair_ms * 1e-3) / 1e12,
+                           "frac": PAIR_THREAD_INST_PER_BEAD * w.n / (pair_ms * 1e-3) / alu_peak,
+                           "unit": "T thread-instructions/s",
+                           "note": "instructions the kernel issues (ncu), against the same peak"},
                 "peak_source": "152 SMs x 128 lanes x %.0f MHz (one op per lane per cycle)"
                                % peaks["sm_max_mhz"]}
     step_ms = ms32 / args.steps
