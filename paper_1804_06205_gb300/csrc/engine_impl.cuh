@@ -532,7 +532,7 @@ class BatchEngine : public BatchBase {
         int cap = (int)std::ceil(mean + 3.0 * std::sqrt(mean) + 8.0);
         cap = (cap + 15) / 16 * 16;
         const int cap_max = (int)((96 * 1024) / (2 * sizeof(vec4)));
-        h.cap = std::max(T_ + 64, std::min(cap, std::min(cap_max, 2016)));
+        h.cap = std::max(64, std::min(cap, std::min(cap_max, 2016)));
     }
 
     // Descriptor, bead -> system and brick -> system maps, a_ij table and

@@ -513,17 +513,14 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs<P> a) {
 // when its box lies at least r_c from the bead.
 //
 // Each warp takes 32 home beads (one per lane) and alternates two phases:
-//   scan     every lane records its hits r^2 < 1 in row and slot order, at
-//            most PAIR_HMAX per pass;
-//   evaluate the lists are compacted level by level (all first hits, then
-//            all second hits, ...) and evaluated 32 at a time, one hit per
-//            lane; each owner appears at most once per level, so the owners'
-//            sums in shared memory are updated level by level without
-//            conflicts, every owner adding its own hits in its own order.
+//   scan     every lane records its hits r^2 < 1 in row and slot order in its
+//            own queue, at most PAIR_HMAX per pass;
+//   evaluate every lane evaluates its own queue in order and adds the pair
+//            forces to its bead's sums in registers.
 // Passes repeat until all 27 cells are done; oversized neighbourhoods are
 // staged in chunks.  Each bead's force is summed in a fixed order, so runs
-// are deterministic; another brick shape changes only the rounding of the
-// frame coordinates.
+// are deterministic; another brick shape changes only the order of the
+// staged rows and so the rounding of the sums.
 // --------------------------------------------------------------------------
 template <class P>
 struct PairArgs {   // one brick's system, as the kernel body uses it
@@ -564,7 +561,7 @@ constexpr int PAIR_MAXX = 64;          // largest brick length (cells)
 constexpr int PAIR_MAXT = 16;          // largest number of bead types
 constexpr int PAIR_HMAX = 24;          // hits per lane per pass (level field: 5 bits)
 constexpr int PAIR_NR = 16;            // staged rows, (2+2) x (2+2)
-static_assert(PAIR_HMAX < 32, "a lane per level holds the compacted level starts");
+static_assert(PAIR_HMAX >= 1 && PAIR_HMAX <= 64, "hit queue length");
 constexpr int PAIR_THREADS_PER_SM = 896; // FP32 register budget: 28 warps per SM
 constexpr int PAIR_PC = 3;             // ints per staged run: source, slot, length
 
@@ -581,10 +578,8 @@ struct PairSmem {
         b += (size_t)ntmax * ntmax * sizeof(real) + PAIR_NR * 2 * sizeof(real);
         b = align16(b);
         const size_t nw = (size_t)T / 32;
-        b += nw * 32 * sizeof(vec4);                               // owners' sums
-        if (sample) b += nw * 32 * sizeof(real);                   // owners' energies
-        b += nw * PAIR_HMAX * 32 * sizeof(uint16_t);               // hit queue
-        b += nw * 32 * sizeof(uint16_t);                           // owners' staged slots
+        b += nw * PAIR_HMAX * 32 * sizeof(uint16_t);               // hit queues
+        (void)sample;
         return b;
     }
 };
@@ -720,10 +715,7 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
     real *s_a = reinterpret_cast<real *>(smem + off);
     real *s_rsh = s_a + la.ntmax * la.ntmax;         // per staged row: y, z frame shift
     off = PairSmem<P>::align16((size_t)((unsigned char *)(s_rsh + 2 * PAIR_NR) - smem));
-    vec4 *s_acc = reinterpret_cast<vec4 *>(smem + off);
-    real *s_acce = reinterpret_cast<real *>(s_acc + NW * 32);   // SAMPLE only
-    uint16_t *s_q = reinterpret_cast<uint16_t *>(s_acce + (SAMPLE ? NW * 32 : 0));
-    uint16_t *s_own = s_q + NW * PAIR_HMAX * 32;   // each owner's staged slot
+    uint16_t *s_q = reinterpret_cast<uint16_t *>(smem + off);   // per-lane hit queues
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     __shared__ __align__(8) uint64_t s_mbar;   // completion of the staging copies
@@ -842,17 +834,7 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
     const uint32_t s_lo = (uint32_t)(unsigned long long)sctr;
     const uint32_t s_hi = (uint32_t)((unsigned long long)sctr >> 32);
     const int nt = a.ntypes;
-    vec4 *my_acc = s_acc + wid * 32;
-    real *my_acce = s_acce + wid * 32;
     uint16_t *my_q = s_q + wid * PAIR_HMAX * 32;
-    uint16_t *my_own = s_own + wid * 32;
-    // The whole neighbourhood usually fits one chunk: owners are then read
-    // from their own staged copies.  Otherwise chunks are staged into the
-    // first cap - 32 NW slots and each warp keeps copies of its owners in the
-    // last 32 NW.
-    const bool one_chunk = S <= cap;
-    const int capc = one_chunk ? cap : cap - 32 * NW;
-    const unsigned lt_mask = (1u << lane) - 1u;
     int staged_lo = -1;
 
     for (int hb0 = 0; hb0 < H; hb0 += T) {
@@ -883,24 +865,16 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
                 hp.z = add_rn(pr.z, mul_rn((real)(-z0), hz));
             }
         }
-        if (one_chunk) {
-            my_own[lane] = (uint16_t)(active ? s_cs[sr_home * W + 1] + (hb - s_hr[4 * hr + 1]) : 0);
-        } else {
-            const int qo = capc + wid * 32 + lane;
-            s_pos[qo] = hp;
-            s_vt[qo] = a.vt[g];
-            my_own[lane] = (uint16_t)qo;
-        }
-        my_acc[lane] = mk4<vec4, real>((real)0, (real)0, (real)0, (real)0);
-        if (SAMPLE) my_acce[lane] = (real)0;
+        const vec4 hv = a.vt[g];
+        real ax = 0, ay = 0, az = 0, aw = 0, ae = 0;   // this bead's sums
         // distances from the bead to the faces of its cell (pruning)
         const real lxd = hp.x - (real)uxi * hx, uxd = hx - lxd;
         const real lyd = hp.y - (real)ry * hy, uyd = hy - lyd;
         const real lzd = hp.z - (real)rz * hz, uzd = hz - lzd;
         const real cut2 = (real)1.0001;
 
-        for (int c0 = 0; c0 < S; c0 += capc) {
-            const int c1 = min(S, c0 + capc);
+        for (int c0 = 0; c0 < S; c0 += cap) {
+            const int c1 = min(S, c0 + cap);
             if (staged_lo != c0) {
                 fence_proxy_async_smem();   // this chunk's reads before the next copies
                 __syncthreads();            // everyone is done with the previous chunk
@@ -1013,86 +987,44 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
                     more = r9 < 9;
                 }
                 __syncwarp();
-                // ---- compact level by level: all first hits, then all second hits,
-                // ...; entries gain the owner lane (slot | owner << 11) and lane m
-                // keeps the start K_m of level m (lane nlev: the total)
-                int K = 0, nlev = 0, myK = 0;
-                for (int m = 0; m < PAIR_HMAX; ++m) {
-                    const unsigned A = __ballot_sync(FULL, nh > m);
-                    if (A == 0u) break;
-                    if (lane == m) myK = K;
-                    uint32_t e = 0;
-                    if (nh > m) e = my_q[m * 32 + lane];
-                    __syncwarp();
-                    if (nh > m) my_q[K + __popc(A & lt_mask)] = (uint16_t)(e | ((uint32_t)lane << 11));
-                    __syncwarp();
-                    K += __popc(A);
-                    nlev = m + 1;
-                }
-                if (lane == nlev) myK = K;
-                // ---- evaluate 32 hits at a time, sums updated level by level
-                for (int b = 0; b < K; b += 32) {
-                    const int f = b + lane;
-                    const bool valid = f < K;
-                    const uint32_t e = valid ? (uint32_t)my_q[f] : 0u;
-                    const int jl = (int)(e & 2047u), owner = (int)(e >> 11);
-                    real fx = 0, fy = 0, fz = 0, wc = 0, ep = 0;
-                    if (valid) {
-                        const int qo = my_own[owner];
-                        const vec4 hpo = s_pos[qo], hvo = s_vt[qo];
+                // ---- evaluate: each lane takes its own hits in scan order and adds
+                // them to its bead's sums in registers
+                const int nmax = (int)__reduce_max_sync(FULL, (unsigned)nh);
+                for (int m = 0; m < nmax; ++m) {
+                    if (m < nh) {
+                        const int jl = my_q[m * 32 + lane];
                         const vec4 pj = s_pos[jl], vj = s_vt[jl];
-                        const real dx = hpo.x - pj.x, dyv = hpo.y - pj.y, dzv = hpo.z - pj.z;
+                        const real dx = xi - pj.x, dyv = yi - pj.y, dzv = zi - pj.z;
                         const real r2 = fma_rn(dzv, dzv, fma_rn(dyv, dyv, mul_rn(dx, dx)));
                         const real rinv = rsqrt_r(r2);
                         const real rr1 = mul_rn(r2, rinv);
                         const real w = (real)1 - rr1;
                         const real ex = mul_rn(dx, rinv), ey = mul_rn(dyv, rinv), ez = mul_rn(dzv, rinv);
-                        const real evel = fma_rn(ez, hvo.z - vj.z,
-                                                 fma_rn(ey, hvo.y - vj.y, mul_rn(ex, hvo.x - vj.x)));
-                        const real aij = s_a[(int)hpo.w * nt + (int)pj.w];
-                        const int32_t idi = P::unpack_id(hvo.w), idj = P::unpack_id(vj.w);
+                        const real evel = fma_rn(ez, hv.z - vj.z,
+                                                 fma_rn(ey, hv.y - vj.y, mul_rn(ex, hv.x - vj.x)));
+                        const real aij = s_a[(int)hp.w * nt + (int)pj.w];
+                        const int32_t idi = P::unpack_id(hv.w), idj = P::unpack_id(vj.w);
                         const uint32_t lo = (uint32_t)min(idi, idj), hi = (uint32_t)max(idi, idj);
                         const uint2 rnd = philox_rk(lo, hi, s_lo, s_hi, rkl);
                         const real th = theta_pair(rnd, a.noise, (real)0);
                         const real fc = mul_rn(aij, w);
                         const real gw2 = mul_rn(mul_rn(a.gamma, w), w);
                         const real mag = fma_rn(mul_rn(a.sig_sqdt, w), th, fma_rn(-gw2, evel, fc));
-                        fx = mul_rn(mag, ex);
-                        fy = mul_rn(mag, ey);
-                        fz = mul_rn(mag, ez);
+                        ax = add_rn(ax, mul_rn(mag, ex));
+                        ay = add_rn(ay, mul_rn(mag, ey));
+                        az = add_rn(az, mul_rn(mag, ez));
                         if (SAMPLE) {
-                            wc = rr1 * fc;
-                            ep = (real)0.5 * fc * w;
+                            aw += rr1 * fc;
+                            ae += (real)0.5 * fc * w;
                         }
-                    }
-                    // the levels this batch spans; a lane's level is the one whose
-                    // range [K_lv, K_lv+1) holds its entry
-                    const int last = min(b + 31, K - 1);
-                    const int lv_lo = __popc(__ballot_sync(FULL, lane <= nlev && myK <= b)) - 1;
-                    const int lv_hi = __popc(__ballot_sync(FULL, lane <= nlev && myK <= last)) - 1;
-                    for (int lv = lv_lo; lv <= lv_hi; ++lv) {
-                        const int klo = __shfl_sync(FULL, myK, lv), khi = __shfl_sync(FULL, myK, lv + 1);
-                        if (valid && f >= klo && f < khi) {
-                            vec4 s = my_acc[owner];
-                            s.x = add_rn(s.x, fx);
-                            s.y = add_rn(s.y, fy);
-                            s.z = add_rn(s.z, fz);
-                            if (SAMPLE) {
-                                s.w += wc;
-                                my_acce[owner] += ep;
-                            }
-                            my_acc[owner] = s;
-                        }
-                        __syncwarp();
                     }
                 }
                 __syncwarp();
             }
         }
         if (active) {
-            const vec4 s = my_acc[lane];
-            a.fpair[g] = mk4<vec4, real>(s.x, s.y, s.z, (real)0);
-            if (SAMPLE) a.ev[g] = mk4<vec4, real>(s.w, my_acce[lane], (real)0, (real)0);
+            a.fpair[g] = mk4<vec4, real>(ax, ay, az, (real)0);
+            if (SAMPLE) a.ev[g] = mk4<vec4, real>(aw, ae, (real)0, (real)0);
         }
         __syncwarp();
     }
