@@ -559,7 +559,7 @@ struct PairLaunch {   // a launch over bricks [br_lo, br_lo + gridDim.x) of any 
 
 constexpr int PAIR_MAXX = 64;          // largest brick length (cells)
 constexpr int PAIR_MAXT = 16;          // largest number of bead types
-constexpr int PAIR_HMAX = 24;          // hits per lane per pass (level field: 5 bits)
+constexpr int PAIR_HMAX = 32;          // hits per lane per pass
 constexpr int PAIR_NR = 16;            // staged rows, (2+2) x (2+2)
 static_assert(PAIR_HMAX >= 1 && PAIR_HMAX <= 64, "hit queue length");
 constexpr int PAIR_THREADS_PER_SM = 896; // FP32 register budget: 28 warps per SM
@@ -835,6 +835,60 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
     const uint32_t s_hi = (uint32_t)((unsigned long long)sctr >> 32);
     const int nt = a.ntypes;
     uint16_t *my_q = s_q + wid * PAIR_HMAX * 32;
+    // Stage slots [c0, c1) of the neighbourhood: bulk copies of each source run,
+    // then every staged cell moved into the brick's frame.  False if a copy
+    // never completed (the block must then leave).
+    auto stage = [&](int c0, int c1) -> bool {
+        fence_proxy_async_smem();   // this chunk's reads before the next copies
+        __syncthreads();            // everyone is done with the previous chunk
+        if (tid < NRe * 3) {        // one thread per source run: positions, v~
+            const int *pc = s_pc + tid * PAIR_PC;
+            const int src = pc[0], dst = pc[1], len = pc[2];
+            const int lo = max(dst, c0), hi = min(dst + len, c1);
+            if (lo < hi) {
+                const uint32_t bytes = (uint32_t)(hi - lo) * (uint32_t)sizeof(vec4);
+                mbar_expect_tx(&s_mbar, 2u * bytes);
+                bulk_g2s(s_pos + (lo - c0), a.pos + src + (lo - dst), bytes, &s_mbar);
+                bulk_g2s(s_vt + (lo - c0), a.vt + src + (lo - dst), bytes, &s_mbar);
+            }
+        }
+        __syncthreads();
+        if (tid == 0) mbar_arrive(&s_mbar);
+        const bool got = mbar_wait_bounded(&s_mbar, mphase, MBAR_TRIES);
+        mphase ^= 1u;
+        if (__syncthreads_or(!got)) {   // a copy never completed: flag it, leave
+            if (tid == 0) atomicOr(la.status, ST_TIMEOUT);
+            mbar_wait_bounded(&s_mbar, mphase ^ 1u, MBAR_TRIES);
+            return false;
+        }
+        // into the brick's frame, cell by cell: x by the cell's place in
+        // the brick, y and z by the row's shift
+        for (int e = tid; e < NRe * W; e += T) {
+            const int r = e / W, k = e - r * W;
+            if (k > Xe + 1) continue;                 // the row-end entry
+            const int lo = max(s_cs[e], c0), hi = min(s_cs[e + 1], c1);
+            if (lo >= hi) continue;
+            real sx;
+            if (P::kOffsets) {
+                sx = (real)(k - 1);
+            } else {   // absolute x -> brick frame, undoing the cell's wrap
+                int cx = x0 + k - 1;
+                cx += cx < 0 ? a.nx : (cx >= a.nx ? -a.nx : 0);
+                sx = mul_rn((real)(k - 1 - cx), hx);
+            }
+            const real sy = s_rsh[2 * r], sz = s_rsh[2 * r + 1];
+            for (int q = lo; q < hi; ++q) {
+                vec4 p = s_pos[q - c0];
+                if (P::kOffsets) p.x = fma_rn(sx, hx, p.x);
+                else p.x = add_rn(p.x, sx);
+                p.y = add_rn(p.y, sy);
+                p.z = add_rn(p.z, sz);
+                s_pos[q - c0] = p;
+            }
+        }
+        __syncthreads();   // staged and moved before anyone scans
+        return true;
+    };
     int staged_lo = -1;
 
     for (int hb0 = 0; hb0 < H; hb0 += T) {
@@ -847,12 +901,19 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
         const int g = active ? s_hr[4 * hr + 3] + (hb - s_hr[4 * hr + 1]) : 0;
         const int ry = hr % 2, rz = hr / 2;
         const int sr_home = s_hr[4 * hr];
-        const vec4 pr = a.pos[g];
+        // this bead's state from global memory; the loads are in flight while
+        // the first chunk is staged
+        const vec4 pr = a.pos[g], hv = a.vt[g];
+        const uint32_t kg = a.key[g];
+        if (staged_lo != 0) {
+            if (!stage(0, min(S, cap))) return;
+            staged_lo = 0;
+        }
         int uxi = 0;
         vec4 hp = pr;
         if (active) {
             const uint32_t rowkey = ((uint32_t)(z0 + rz) * a.ny + (y0 + ry)) * a.nx;
-            uxi = (int)(a.key[g] - rowkey) - x0;
+            uxi = (int)(kg - rowkey) - x0;
             // the same operations as the staging of this bead's own copy, so the
             // two coincide bit for bit and the self pair has r^2 == 0 exactly
             if (P::kOffsets) {
@@ -865,7 +926,6 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
                 hp.z = add_rn(pr.z, mul_rn((real)(-z0), hz));
             }
         }
-        const vec4 hv = a.vt[g];
         real ax = 0, ay = 0, az = 0, aw = 0, ae = 0;   // this bead's sums
         // distances from the bead to the faces of its cell (pruning)
         const real lxd = hp.x - (real)uxi * hx, uxd = hx - lxd;
@@ -876,55 +936,8 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
         for (int c0 = 0; c0 < S; c0 += cap) {
             const int c1 = min(S, c0 + cap);
             if (staged_lo != c0) {
-                fence_proxy_async_smem();   // this chunk's reads before the next copies
-                __syncthreads();            // everyone is done with the previous chunk
-                if (tid < NRe * 3) {        // one thread per source run: positions, v~
-                    const int *pc = s_pc + tid * PAIR_PC;
-                    const int src = pc[0], dst = pc[1], len = pc[2];
-                    const int lo = max(dst, c0), hi = min(dst + len, c1);
-                    if (lo < hi) {
-                        const uint32_t bytes = (uint32_t)(hi - lo) * (uint32_t)sizeof(vec4);
-                        mbar_expect_tx(&s_mbar, 2u * bytes);
-                        bulk_g2s(s_pos + (lo - c0), a.pos + src + (lo - dst), bytes, &s_mbar);
-                        bulk_g2s(s_vt + (lo - c0), a.vt + src + (lo - dst), bytes, &s_mbar);
-                    }
-                }
-                __syncthreads();
-                if (tid == 0) mbar_arrive(&s_mbar);
-                const bool got = mbar_wait_bounded(&s_mbar, mphase, MBAR_TRIES);
-                mphase ^= 1u;
-                if (__syncthreads_or(!got)) {   // a copy never completed: flag it, leave
-                    if (tid == 0) atomicOr(la.status, ST_TIMEOUT);
-                    mbar_wait_bounded(&s_mbar, mphase ^ 1u, MBAR_TRIES);
-                    return;
-                }
-                // into the brick's frame, cell by cell: x by the cell's place in
-                // the brick, y and z by the row's shift
-                for (int e = tid; e < NRe * W; e += T) {
-                    const int r = e / W, k = e - r * W;
-                    if (k > Xe + 1) continue;                 // the row-end entry
-                    const int lo = max(s_cs[e], c0), hi = min(s_cs[e + 1], c1);
-                    if (lo >= hi) continue;
-                    real sx;
-                    if (P::kOffsets) {
-                        sx = (real)(k - 1);
-                    } else {   // absolute x -> brick frame, undoing the cell's wrap
-                        int cx = x0 + k - 1;
-                        cx += cx < 0 ? a.nx : (cx >= a.nx ? -a.nx : 0);
-                        sx = mul_rn((real)(k - 1 - cx), hx);
-                    }
-                    const real sy = s_rsh[2 * r], sz = s_rsh[2 * r + 1];
-                    for (int q = lo; q < hi; ++q) {
-                        vec4 p = s_pos[q - c0];
-                        if (P::kOffsets) p.x = fma_rn(sx, hx, p.x);
-                        else p.x = add_rn(p.x, sx);
-                        p.y = add_rn(p.y, sy);
-                        p.z = add_rn(p.z, sz);
-                        s_pos[q - c0] = p;
-                    }
-                }
+                if (!stage(c0, c1)) return;
                 staged_lo = c0;
-                __syncthreads();
             }
             __syncwarp();
             const real xi = hp.x, yi = hp.y, zi = hp.z;
