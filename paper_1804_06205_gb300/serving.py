@@ -53,14 +53,18 @@ def tile_for(table: Optional[dict], L) -> int:
 
 
 class Server:
-    """precision 0 = FP32 path, 1 = FP64 path; table = autotuner output."""
+    """precision 0 = FP32 path, 1 = FP64 path; table = autotuner output;
+    use_graph: replay each step shape as a CUDA graph or launch the kernels
+    directly (the default: admissions and departures come every few chunks
+    and each would force the graphs to be captured again, which costs more
+    than the launches they save)."""
 
     def __init__(self, max_beads=2_000_000, max_cells=2_000_000, max_bonds=1_000_000,
                  max_systems=128, chunk=50, precision=0, table=None, keep_states=False,
-                 clock=time.perf_counter, cuda_stream=None):
+                 clock=time.perf_counter, cuda_stream=None, use_graph=False):
         from . import dpd as D          # loads libdpd.so, fails loudly if it is not built
         threads = int(table.get("threads", 0)) if table else 0
-        opts = dict(precision=precision, threads=threads)
+        opts = dict(precision=precision, threads=threads, use_graph=1 if use_graph else 0)
         if cuda_stream is not None:
             opts["cuda_stream"] = cuda_stream
         self.batch = D.Batch(max_beads, max_cells, max_bonds, max_systems=max_systems, **opts)
