@@ -341,9 +341,10 @@ __global__ void __launch_bounds__(256) k_init(InitArgs<P> a) {
 }
 
 // --------------------------------------------------------------------------
-// a3: counting sort.  Exclusive scan of the per-cell counts in three passes
-// (block sums, scan of block sums, block scans plus offsets); the third pass
-// also clears the counts for the next step.
+// a3: counting sort.  Exclusive scan of the per-cell counts: block sums
+// (k_scan1), then block scans plus the sum of the preceding blocks
+// (k_scan3b), which also clears the counts for the next step.  k_scan2 scans
+// the block sums in one block for the allocation-free cell division.
 // --------------------------------------------------------------------------
 constexpr int SCAN_T = 256, SCAN_V = 8, SCAN_B = SCAN_T * SCAN_V;
 

@@ -394,3 +394,35 @@ def test_full_size_fluid_3m_sampled_parity(D, prec):
     scale = np.abs(fo).max()
     assert np.abs(f[idx] - fo).max() <= TOL[prec] * scale
     assert np.abs(f.sum(axis=0)).max() < (1e-2 if prec == FP32 else 1e-6) * np.sqrt(w.n)
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+@pytest.mark.parametrize("name", ["melt_98k", "peptide_192k"])
+def test_full_size_configs_match_oracle(D, prec, name):
+    """The polymer melt (32^3, 98,304 beads, 88,470 harmonic bonds) and the
+    peptide-like system (40^3, 192,000 beads, harmonic and standard-Morse
+    bonds) at full size with default options: every bead's force from an
+    identical state, and every bead after 3 steps, against the oracle's
+    cell-list sum (equal to its brute-force sum to 1e-12)."""
+    w = W.make(name)
+    s = osys(w)
+    g = gsys(D, w, prec)
+    g.set_state(w.pos, w.vel, 3)
+    f = g.get_state()[2]
+    fo, _ = O.forces(s, O.wrap(s, w.pos), w.vel, 3, mode=O.MODE_CELLS)
+    scale = np.abs(fo).max()
+    assert np.abs(f - fo).max() <= TOL[prec] * scale
+    g.step(3)
+    pos, vel, _, step = g.get_state()
+    g.close()
+    st = O.State(s, w.pos, w.vel, 3, mode=O.MODE_CELLS)
+    st.run(3)
+    assert step == st.step == 6
+    d = pos - st.pos
+    d -= w.L * np.round(d / w.L)
+    # positions: FP32 keeps offsets inside unit cells (resolution ~1e-7) and
+    # the stiffest bonds (max |f| ~ 7.5e3 in the peptide system) amplify force
+    # rounding by dt^2 per step; velocities: a force error e changes v by dt e
+    # per step, with the one-evaluation tolerance as e
+    assert np.abs(d).max() < (1e-4 if prec == FP32 else 1e-11)
+    assert np.abs(vel - st.vel).max() <= 4 * w.dt * TOL[prec] * scale
