@@ -64,13 +64,13 @@ PAIR_OPS_PER_BEAD = 40.5 * 7 + 6.28 * 103
 SORT_BYTES_PER_BEAD = 172.0
 # DRAM bytes (read + written) per bead of one k_pair launch, from an ncu
 # capture of the current pair kernel on the 70^3 fluid (dram__bytes_read.sum +
-# dram__bytes_write.sum = 39.26 MB for 1,029,000 beads); the launch's force
+# dram__bytes_write.sum = 39.39 MB for 1,029,000 beads); the launch's force
 # writes stay in L2 and reach DRAM in later kernels.
-PAIR_DRAM_BYTES_PER_BEAD = 38.15
+PAIR_DRAM_BYTES_PER_BEAD = 38.28
 # Thread instructions executed per bead by one k_pair launch, from the same
 # capture (smsp__inst_executed.sum x thread_inst_executed_per_inst_executed):
 # the issued work, against which the issue-rate roofline is taken.
-PAIR_THREAD_INST_PER_BEAD = 4948.0
+PAIR_THREAD_INST_PER_BEAD = 4911.0
 BOND_BYTES_PER_BEAD = 144.0
 
 

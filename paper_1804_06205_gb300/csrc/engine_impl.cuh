@@ -300,10 +300,11 @@ class BatchEngine : public BatchBase {
         const size_t n = (size_t)h.n;
         int rc = ensure_io(n);
         if (rc) return rc;
+        k_inv_perm<<<blocks(h.n), 256, 0, stream_>>>(h.bead0, h.n, id_[cur_], inv_perm_);
         k_unpermute<P><<<blocks(h.n), 256, 0, stream_>>>(s, sys_, pos_, key_, vel_[cur_],
-                                                         frc_[cur_], id_[cur_], io_, io_ + 3 * n,
+                                                         frc_[cur_], inv_perm_, io_, io_ + 3 * n,
                                                          io_ + 6 * n);
-        ++launches_;
+        launches_ += 2;
         DPD_CU(cudaGetLastError());
         if (pos)
             DPD_CU(cudaMemcpyAsync(pos, io_, 3 * n * sizeof(double), cudaMemcpyDeviceToHost,

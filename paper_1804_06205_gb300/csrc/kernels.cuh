@@ -40,8 +40,9 @@ namespace dpd {
 //   PF32: positions are FP32 offsets inside the bead's cell (x = c h + o),
 //         forces and velocities FP32.
 //   PF64: positions are absolute FP64 coordinates, everything FP64.
-// Element w of a position holds the bead type (a small integer value); w of
-// v~ holds the bead id (bit pattern).
+// Element w of a position holds the bead type and w of v~ the bead id, both
+// as the bit pattern of the integer (pack_int), so no conversion is spent on
+// them in the pair loop.
 // --------------------------------------------------------------------------
 struct __align__(32) dvec4 {
     double x, y, z, w;
@@ -51,18 +52,18 @@ struct PF32 {
     using real = float;
     using vec4 = float4;
     static constexpr bool kOffsets = true;
-    static __device__ __forceinline__ real pack_id(int32_t i) { return __int_as_float(i); }
-    static __device__ __forceinline__ int32_t unpack_id(real w) { return __float_as_int(w); }
+    static __device__ __forceinline__ real pack_int(int32_t i) { return __int_as_float(i); }
+    static __device__ __forceinline__ int32_t unpack_int(real w) { return __float_as_int(w); }
 };
 
 struct PF64 {
     using real = double;
     using vec4 = dvec4;
     static constexpr bool kOffsets = false;
-    static __device__ __forceinline__ real pack_id(int32_t i) {
+    static __device__ __forceinline__ real pack_int(int32_t i) {
         return __longlong_as_double((long long)i);
     }
-    static __device__ __forceinline__ int32_t unpack_id(real w) {
+    static __device__ __forceinline__ int32_t unpack_int(real w) {
         return (int32_t)__double_as_longlong(w);
     }
 };
@@ -101,7 +102,9 @@ __device__ __forceinline__ uint2 philox_xy(uint32_t c0, uint32_t c1, uint32_t c2
 
 // Uniform (2*(x>>9)+1) * 2^-24 in (0, 1), exact in binary32.
 __device__ __forceinline__ float u01_f32(uint32_t x) {
-    return __uint2float_rn((x >> 8) | 1u) * 0x1p-24f;
+    // ((x >> 8) | 1) * 2^-24 built without an int->float conversion: 1 + (x>>9)
+    // 2^-23 by its bits, minus 1 and plus 2^-24, both exact
+    return __fadd_rn(__fsub_rn(__uint_as_float(0x3F800000u | (x >> 9)), 1.0f), 0x1p-24f);
 }
 __device__ __forceinline__ double u01_f64(uint32_t x) {
     return (double)((x >> 8) | 1u) * 0x1p-24;
@@ -329,7 +332,7 @@ __global__ void __launch_bounds__(256) k_init(InitArgs<P> a) {
     typename P::vec4 out;
     uint32_t key;
     place_bead<P>(D, a.pos_in[3 * i], a.pos_in[3 * i + 1], a.pos_in[3 * i + 2],
-                  (real)a.types[i], out, key, a.status, ST_BADINPUT);
+                  P::pack_int(a.types[i]), out, key, a.status, ST_BADINPUT);
     a.pos_tmp[t] = out;
     a.key_tmp[t] = key;
     a.rank[t] = atomicAdd(&a.count[D.cell0 + key], 1u);
@@ -498,7 +501,7 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs<P> a) {
     if (a.inv_perm) a.inv_perm[D.bead0 + i] = u;
     // Fig. 1 step 2: velocity predictor used by the dissipative force
     a.vt[u] = mk4<typename P::vec4, typename P::real>(v.x + lam_dt * f.x, v.y + lam_dt * f.y,
-                                                      v.z + lam_dt * f.z, P::pack_id(i));
+                                                      v.z + lam_dt * f.z, P::pack_int(i));
 }
 
 // --------------------------------------------------------------------------
@@ -1016,8 +1019,8 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
                         const real ex = mul_rn(dx, rinv), ey = mul_rn(dyv, rinv), ez = mul_rn(dzv, rinv);
                         const real evel = fma_rn(ez, hv.z - vj.z,
                                                  fma_rn(ey, hv.y - vj.y, mul_rn(ex, hv.x - vj.x)));
-                        const real aij = s_a[(int)hp.w * nt + (int)pj.w];
-                        const int32_t idi = P::unpack_id(hv.w), idj = P::unpack_id(vj.w);
+                        const real aij = s_a[P::unpack_int(hp.w) * nt + P::unpack_int(pj.w)];
+                        const int32_t idi = P::unpack_int(hv.w), idj = P::unpack_int(vj.w);
                         const uint32_t lo = (uint32_t)min(idi, idj), hi = (uint32_t)max(idi, idj);
                         const uint2 rnd = philox_rk(lo, hi, s_lo, s_hi, rkl);
                         const real th = theta_pair(rnd, a.noise, (real)0);
@@ -1250,18 +1253,28 @@ __global__ void k_reduce_final(const int4 *rsys, const SysDesc<P> *sys, const do
 // --------------------------------------------------------------------------
 // State read-back and the cell-division inspection (one system).
 // --------------------------------------------------------------------------
+// id -> slot map of one system's beads, for the gathering read-out below
+static __global__ void __launch_bounds__(256) k_inv_perm(int bead0, int n, const int32_t *id,
+                                                         int32_t *inv_perm) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    inv_perm[bead0 + id[bead0 + k]] = bead0 + k;
+}
+
+// One system's state in bead-id order, as doubles: thread i gathers bead i
+// from its slot (so the writes are contiguous), with absolute positions.
 template <class P>
 __global__ void __launch_bounds__(256) k_unpermute(int s, const SysDesc<P> *sys,
                                                    const typename P::vec4 *pos,
                                                    const uint32_t *key,
                                                    const typename P::vec4 *vel,
-                                                   const typename P::vec4 *frc, const int32_t *id,
+                                                   const typename P::vec4 *frc,
+                                                   const int32_t *inv_perm,
                                                    double *opos, double *ovel, double *ofrc) {
     const SysDesc<P> &D = sys[s];
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= D.n) return;
-    const int t = D.bead0 + k;
-    const int i = id[t];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= D.n) return;
+    const int t = inv_perm[D.bead0 + i];
     const typename P::vec4 p = pos[t], v = vel[t], f = frc[t];
     double x = p.x, y = p.y, z = p.z;
     if (P::kOffsets) {
