@@ -62,6 +62,9 @@ class BatchEngine : public BatchBase {
         for (cudaEvent_t e : prof_ev_) cudaEventDestroy(e);
         for (cudaEvent_t e : ph_)
             if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : xev_)
+            if (e) cudaEventDestroy(e);
+        if (xfer_) cudaStreamDestroy(xfer_);
         for (void *p : allocs_) cudaFree(p);
         if (own_stream_ && stream_) cudaStreamDestroy(stream_);
     }
@@ -89,6 +92,7 @@ class BatchEngine : public BatchBase {
             (rc = alloc(&key_, N)) || (rc = alloc(&key_tmp_, N)) || (rc = alloc(&rank_, N)) ||
             (rc = alloc(&src_, N)) || (rc = alloc(&sid_, N)) || (rc = alloc(&id_[0], N)) ||
             (rc = alloc(&id_[1], N)) || (rc = alloc(&inv_perm_, N)) || (rc = alloc(&bsys_, N)) ||
+            (rc = alloc(&types_, N)) ||
             (rc = alloc(&count_, C)) || (rc = alloc(&cell_start_, C + 1)) ||
             (rc = alloc(&bsum_, C / SCAN_B + 2)) || (rc = alloc(&brick_sys_, (size_t)NBR_)) ||
             (rc = alloc(&sys_, (size_t)NS_)) || (rc = alloc(&counter_, (size_t)NS_)) ||
@@ -100,6 +104,8 @@ class BatchEngine : public BatchBase {
             (rc = alloc(&old_bead0_, (size_t)NS_)))
             return rc;
         for (auto &e : ph_) DPD_CU(cudaEventCreate(&e));
+        for (auto &e : xev_) DPD_CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        DPD_CU(cudaStreamCreateWithFlags(&xfer_, cudaStreamNonBlocking));
         DPD_CU(cudaMemsetAsync(count_, 0, C * sizeof(uint32_t), stream_));
         DPD_CU(cudaMemsetAsync(status_, 0, sizeof(int), stream_));
         DPD_CU(cudaMemsetAsync(acc_, 0, (size_t)NS_ * 4 * sizeof(double), stream_));
@@ -219,12 +225,6 @@ class BatchEngine : public BatchBase {
         SysHost &h = hs_[s];
         const size_t n = (size_t)h.n;
         if ((rc = ensure_io(n))) return rc;
-        DPD_CU(cudaMemcpyAsync(io_, pos, 3 * n * sizeof(double), cudaMemcpyHostToDevice, stream_));
-        DPD_CU(cudaMemcpyAsync(io_ + 3 * n, vel, 3 * n * sizeof(double), cudaMemcpyHostToDevice,
-                               stream_));
-        int32_t *types_d = reinterpret_cast<int32_t *>(io_ + 6 * n);
-        DPD_CU(cudaMemcpyAsync(types_d, h.cfg.types.data(), n * sizeof(int32_t),
-                               cudaMemcpyHostToDevice, stream_));
         // the initial binning writes the "old" buffers; the sort brings the
         // system into the current ones, leaving the other systems untouched
         const int old = cur_ ^ 1;
@@ -233,7 +233,7 @@ class BatchEngine : public BatchBase {
         ia.sys = sys_;
         ia.pos_in = io_;
         ia.vel_in = io_ + 3 * n;
-        ia.types = types_d;
+        ia.types = types_ + h.bead0;
         ia.pos_tmp = pos_tmp_;
         ia.vel = vel_[old];
         ia.frc = frc_[old];
@@ -242,9 +242,25 @@ class BatchEngine : public BatchBase {
         ia.count = count_;
         ia.id = id_[old];
         ia.status = status_;
-        k_init<P><<<blocks(h.n), 256, 0, stream_>>>(ia);
-        ++launches_;
-        DPD_CU(cudaGetLastError());
+        // host -> device in chunks on the copy stream, each binned as soon as
+        // it has arrived; the copies wait for earlier work on io_
+        const int nch = io_chunks(h.n);
+        DPD_CU(cudaEventRecord(xev_[IO_MAXCH], stream_));
+        DPD_CU(cudaStreamWaitEvent(xfer_, xev_[IO_MAXCH], 0));
+        for (int c = 0; c < nch; ++c) {
+            const size_t i0 = (size_t)h.n * c / nch, i1 = (size_t)h.n * (c + 1) / nch;
+            DPD_CU(cudaMemcpyAsync(io_ + 3 * i0, pos + 3 * i0, 3 * (i1 - i0) * sizeof(double),
+                                   cudaMemcpyHostToDevice, xfer_));
+            DPD_CU(cudaMemcpyAsync(io_ + 3 * n + 3 * i0, vel + 3 * i0,
+                                   3 * (i1 - i0) * sizeof(double), cudaMemcpyHostToDevice, xfer_));
+            DPD_CU(cudaEventRecord(xev_[c], xfer_));
+            DPD_CU(cudaStreamWaitEvent(stream_, xev_[c], 0));
+            ia.i0 = (int)i0;
+            ia.i1 = (int)i1;
+            k_init<P><<<blocks((int)(i1 - i0)), 256, 0, stream_>>>(ia);
+            ++launches_;
+            DPD_CU(cudaGetLastError());
+        }
         long long sv = (long long)step;
         DPD_CU(cudaMemcpyAsync(counter_ + s, &sv, sizeof(long long), cudaMemcpyHostToDevice,
                                stream_));
@@ -301,20 +317,32 @@ class BatchEngine : public BatchBase {
         int rc = ensure_io(n);
         if (rc) return rc;
         k_inv_perm<<<blocks(h.n), 256, 0, stream_>>>(h.bead0, h.n, id_[cur_], inv_perm_);
-        k_unpermute<P><<<blocks(h.n), 256, 0, stream_>>>(s, sys_, pos_, key_, vel_[cur_],
-                                                         frc_[cur_], inv_perm_, io_, io_ + 3 * n,
-                                                         io_ + 6 * n);
-        launches_ += 2;
+        ++launches_;
         DPD_CU(cudaGetLastError());
-        if (pos)
-            DPD_CU(cudaMemcpyAsync(pos, io_, 3 * n * sizeof(double), cudaMemcpyDeviceToHost,
-                                   stream_));
-        if (vel)
-            DPD_CU(cudaMemcpyAsync(vel, io_ + 3 * n, 3 * n * sizeof(double),
-                                   cudaMemcpyDeviceToHost, stream_));
-        if (force)
-            DPD_CU(cudaMemcpyAsync(force, io_ + 6 * n, 3 * n * sizeof(double),
-                                   cudaMemcpyDeviceToHost, stream_));
+        // read out in chunks of ids, each copied to the host on the copy stream
+        // while the next one is gathered
+        const int nch = io_chunks(h.n);
+        for (int c = 0; c < nch; ++c) {
+            const size_t i0 = (size_t)h.n * c / nch, i1 = (size_t)h.n * (c + 1) / nch;
+            k_unpermute<P><<<blocks((int)(i1 - i0)), 256, 0, stream_>>>(
+                s, (int)i0, (int)i1, sys_, pos_, key_, vel_[cur_], frc_[cur_], inv_perm_, io_,
+                io_ + 3 * n, io_ + 6 * n);
+            ++launches_;
+            DPD_CU(cudaGetLastError());
+            DPD_CU(cudaEventRecord(xev_[c], stream_));
+            DPD_CU(cudaStreamWaitEvent(xfer_, xev_[c], 0));
+            const size_t b = 3 * (i1 - i0) * sizeof(double);
+            if (pos)
+                DPD_CU(cudaMemcpyAsync(pos + 3 * i0, io_ + 3 * i0, b, cudaMemcpyDeviceToHost,
+                                       xfer_));
+            if (vel)
+                DPD_CU(cudaMemcpyAsync(vel + 3 * i0, io_ + 3 * n + 3 * i0, b,
+                                       cudaMemcpyDeviceToHost, xfer_));
+            if (force)
+                DPD_CU(cudaMemcpyAsync(force + 3 * i0, io_ + 6 * n + 3 * i0, b,
+                                       cudaMemcpyDeviceToHost, xfer_));
+        }
+        DPD_CU(cudaStreamSynchronize(xfer_));
         DPD_CU(cudaStreamSynchronize(stream_));
         if (step) *step = h.step;
         return check_status();
@@ -482,6 +510,9 @@ class BatchEngine : public BatchBase {
 
     static int blocks(int n, int t = 256) { return std::max(1, (n + t - 1) / t); }
 
+    // chunks of a host <-> device state transfer: at least IO_CHUNK beads each
+    static int io_chunks(int n) { return std::max(1, std::min(IO_MAXCH, n / IO_CHUNK)); }
+
     int peek_status() { return status_host_; }
 
     int check_status() {
@@ -594,6 +625,9 @@ class BatchEngine : public BatchBase {
         std::vector<int32_t> bp(c.bptr.begin(), c.bptr.end());
         for (auto &v : bp) v += h.bond0;
         DPD_CU(cudaMemcpyAsync(bptr_ + h.bead0, bp.data(), bp.size() * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, stream_));
+        // bead types in id order, resident for every later set_state
+        DPD_CU(cudaMemcpyAsync(types_ + h.bead0, c.types.data(), (size_t)h.n * sizeof(int32_t),
                                cudaMemcpyHostToDevice, stream_));
         const size_t nb = c.bpartner.size();
         std::vector<vec4> par(nb);
@@ -807,7 +841,7 @@ class BatchEngine : public BatchBase {
     int enqueue_reduce(int r0, int nr, int k0, int nk, bool accumulate) {
         if (nr <= 0 || nk <= 0) return DPD_OK;
         k_reduce<P><<<nr, RED_T, 0, stream_>>>(rmap_ + r0, vel_[cur_], ev_, partial_ + r0 * RED_K);
-        k_reduce_final<P><<<nk, 32, 0, stream_>>>(rsys_ + k0, sys_, partial_, obs_, acc_,
+        k_reduce_final<P><<<nk, RED_T, 0, stream_>>>(rsys_ + k0, sys_, partial_, obs_, acc_,
                                                   accumulate ? 1 : 0, status_);
         launches_ += 2;
         DPD_CU(cudaGetLastError());
@@ -962,6 +996,9 @@ class BatchEngine : public BatchBase {
     int NB_ = 0, NC_ = 0, NBR_ = 0, NBD_ = 0, NS_ = 0, NRB_ = 0, T_ = 128;
     cudaStream_t stream_ = nullptr;
     bool own_stream_ = false;
+    static constexpr int IO_MAXCH = 8, IO_CHUNK = 1 << 18;
+    cudaStream_t xfer_ = nullptr;          // host <-> device state copies
+    cudaEvent_t xev_[IO_MAXCH + 1] = {};
     std::vector<void *> allocs_;
     std::vector<SysHost> hs_;
     std::vector<SysDesc<P>> hsys_;
@@ -973,7 +1010,7 @@ class BatchEngine : public BatchBase {
     vec4 *pos_ = nullptr, *pos_tmp_ = nullptr, *vel_[2] = {nullptr, nullptr},
          *frc_[2] = {nullptr, nullptr}, *vt_ = nullptr, *fpair_ = nullptr, *ev_ = nullptr;
     uint32_t *key_ = nullptr, *key_tmp_ = nullptr, *rank_ = nullptr, *src_ = nullptr;
-    int32_t *sid_ = nullptr, *id_[2] = {nullptr, nullptr}, *inv_perm_ = nullptr;
+    int32_t *sid_ = nullptr, *id_[2] = {nullptr, nullptr}, *inv_perm_ = nullptr, *types_ = nullptr;
     int *bsys_ = nullptr, *brick_sys_ = nullptr, *old_bead0_ = nullptr;
     uint32_t *count_ = nullptr, *cell_start_ = nullptr, *bsum_ = nullptr;
     SysDesc<P> *sys_ = nullptr;

@@ -320,14 +320,15 @@ struct InitArgs {
     uint32_t *key_tmp, *rank, *count;
     int32_t *id;
     int *status;
+    int i0, i1;                      // the bead ids [i0, i1) of this launch
 };
 
 template <class P>
 __global__ void __launch_bounds__(256) k_init(InitArgs<P> a) {
     using real = typename P::real;
     const SysDesc<P> &D = a.sys[a.s];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= D.n) return;
+    const int i = a.i0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.i1) return;
     const int t = D.bead0 + i;
     typename P::vec4 out;
     uint32_t key;
@@ -1221,15 +1222,32 @@ __global__ void __launch_bounds__(RED_T) k_reduce(const int2 *rmap, const typena
 // sums halved: every pair / bond was visited from both ends).
 // acc[s*4 + 0..2]: sum of kT, sum of p_total, number of samples.
 template <class P>
-__global__ void k_reduce_final(const int4 *rsys, const SysDesc<P> *sys, const double *partial,
-                               double *obs, double *acc, int accumulate, int *status) {
+__global__ void __launch_bounds__(RED_T)
+    k_reduce_final(const int4 *rsys, const SysDesc<P> *sys, const double *partial, double *obs,
+                   double *acc, int accumulate, int *status) {
     const int4 q = rsys[blockIdx.x];
     const int s = q.x;
+    // every thread sums a strided share of the system's block partials, then
+    // the block combines them (fixed order: the result does not depend on timing)
+    double x[RED_K] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = q.y + (int)threadIdx.x; b < q.y + q.z; b += RED_T)
+#pragma unroll
+        for (int k = 0; k < RED_K; ++k) x[k] += partial[b * RED_K + k];
+    __shared__ double sh[RED_T / 32][RED_K];
     __shared__ double r[RED_K];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < RED_K; ++k) {
+        double v = x[k];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[wid][k] = v;
+    }
+    __syncthreads();
     if (threadIdx.x < RED_K) {
-        double x = 0;
-        for (int b = q.y; b < q.y + q.z; ++b) x += partial[b * RED_K + threadIdx.x];
-        r[threadIdx.x] = threadIdx.x >= 4 ? 0.5 * x : x;
+        double v = 0;
+        for (int w = 0; w < RED_T / 32; ++w) v += sh[w][threadIdx.x];
+        r[threadIdx.x] = threadIdx.x >= 4 ? 0.5 * v : v;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1261,10 +1279,11 @@ static __global__ void __launch_bounds__(256) k_inv_perm(int bead0, int n, const
     inv_perm[bead0 + id[bead0 + k]] = bead0 + k;
 }
 
-// One system's state in bead-id order, as doubles: thread i gathers bead i
-// from its slot (so the writes are contiguous), with absolute positions.
+// One system's state in bead-id order, as doubles, for the ids [i0, i1):
+// thread i gathers bead i from its slot (so the writes are contiguous), with
+// absolute positions.
 template <class P>
-__global__ void __launch_bounds__(256) k_unpermute(int s, const SysDesc<P> *sys,
+__global__ void __launch_bounds__(256) k_unpermute(int s, int i0, int i1, const SysDesc<P> *sys,
                                                    const typename P::vec4 *pos,
                                                    const uint32_t *key,
                                                    const typename P::vec4 *vel,
@@ -1272,8 +1291,8 @@ __global__ void __launch_bounds__(256) k_unpermute(int s, const SysDesc<P> *sys,
                                                    const int32_t *inv_perm,
                                                    double *opos, double *ovel, double *ofrc) {
     const SysDesc<P> &D = sys[s];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= D.n) return;
+    const int i = i0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= i1) return;
     const int t = inv_perm[D.bead0 + i];
     const typename P::vec4 p = pos[t], v = vel[t], f = frc[t];
     double x = p.x, y = p.y, z = p.z;
