@@ -210,6 +210,19 @@ int dpd_cells_noalloc(const double *pos_dev, int64_t n, const dpd_box *box, uint
 /* Free the handle and its device memory (NULL is allowed). */
 int dpd_destroy(dpd_handle *h);
 
+/* Check of the failure detection on device waits, without a fault.  One block
+ * waits on an mbarrier for 16 bytes with the bounded poll loop of the pair
+ * kernel's staging wait (each poll is an mbarrier.try_wait).  deliver != 0:
+ * a bulk copy delivers the bytes, the wait completes, the call returns DPD_OK.
+ * deliver == 0: nothing delivers them, the wait gives up after `tries` polls,
+ * the block records the timeout and returns, and the call returns
+ * DPD_ETIMEOUT; no copy is in flight, so the CUDA context stays usable.
+ * tries in [1, DPD_WAIT_CHECK_MAX_TRIES] (else DPD_EINVAL); cuda_stream: NULL =
+ * the legacy default stream.  Allocates nothing; synchronises the stream;
+ * DPD_ECUDA if a CUDA call fails. */
+#define DPD_WAIT_CHECK_MAX_TRIES (1 << 22)
+int dpd_wait_check(int32_t deliver, int32_t tries, void *cuda_stream);
+
 /* ---- batches: many independent systems advanced by the same launches ----
  * A batch owns fixed pools sized at creation.  Systems are added (with their
  * state) and removed at any time between steps; dpd_batch_step advances

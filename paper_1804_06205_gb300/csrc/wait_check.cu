@@ -1,0 +1,58 @@
+// dpd_wait_check: failure detection of the bounded device waits, exercised
+// without a fault.  One block waits on an mbarrier with the same bounded poll
+// loop as the pair kernel's staging wait.  With deliver = 1 a bulk copy brings
+// the 16 bytes the barrier expects and the phase completes; with deliver = 0
+// nothing is copied, the phase can never complete, the wait gives up after
+// `tries` polls and the block records ST_TIMEOUT and returns.  No copy is ever
+// left in flight, so the context stays usable.  The source and the status word
+// are file-scope device variables: the call allocates nothing.
+#include <cuda_runtime.h>
+
+#include "dpd.h"
+#include "kernels.cuh"
+
+namespace {
+
+static __device__ __align__(16) unsigned char g_wc_src[16];
+static __device__ int g_wc_status;
+
+__global__ void k_wait_check(int deliver, int tries) {
+    __shared__ __align__(16) unsigned char buf[16];
+    __shared__ __align__(8) uint64_t mbar;
+    if (threadIdx.x == 0) {
+        dpd::mbar_init(&mbar, 1);
+        dpd::fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        dpd::mbar_expect_tx(&mbar, 16u);
+        if (deliver) dpd::bulk_g2s(buf, g_wc_src, 16u, &mbar);
+        dpd::mbar_arrive(&mbar);
+    }
+    const bool got = dpd::mbar_wait_bounded(&mbar, 0u, tries);
+    if (__syncthreads_or(!got)) {
+        if (threadIdx.x == 0) atomicOr(&g_wc_status, dpd::ST_TIMEOUT);
+        return;
+    }
+    if (threadIdx.x == 0 && buf[0] != g_wc_src[0]) atomicOr(&g_wc_status, dpd::ST_BADINPUT);
+}
+
+}  // namespace
+
+extern "C" int dpd_wait_check(int32_t deliver, int32_t tries, void *cuda_stream) {
+    if (tries <= 0 || tries > DPD_WAIT_CHECK_MAX_TRIES) return DPD_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int zero = 0;
+    if (cudaMemcpyToSymbolAsync(g_wc_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+        return DPD_ECUDA;
+    k_wait_check<<<1, 32, 0, st>>>(deliver ? 1 : 0, tries);
+    if (cudaGetLastError() != cudaSuccess) return DPD_ECUDA;
+    int status = 0;
+    if (cudaMemcpyFromSymbolAsync(&status, g_wc_status, sizeof(int), 0, cudaMemcpyDeviceToHost,
+                                  st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return DPD_ECUDA;
+    if (status & dpd::ST_TIMEOUT) return DPD_ETIMEOUT;
+    return status ? DPD_ECUDA : DPD_OK;
+}

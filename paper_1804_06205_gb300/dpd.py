@@ -36,7 +36,7 @@ EXPORTED = ("dpd_default_options", "dpd_create", "dpd_set_state", "dpd_step", "d
             "dpd_batch_add", "dpd_batch_remove", "dpd_batch_step", "dpd_batch_get_state",
             "dpd_batch_observables", "dpd_batch_usage", "dpd_batch_sync", "dpd_batch_launch_count",
             "dpd_batch_last_error", "dpd_batch_destroy", "dpd_batch_profile_begin",
-            "dpd_batch_profile_end")
+            "dpd_batch_profile_end", "dpd_wait_check")
 
 
 class dpd_box(C.Structure):
@@ -106,6 +106,8 @@ def _load():
     lib.dpd_last_error.argtypes = [P]
     lib.dpd_last_error.restype = C.c_char_p
     lib.dpd_cells_noalloc.argtypes = [P, C.c_int64, P, P, P, P, P]
+    lib.dpd_wait_check.argtypes = [C.c_int32, C.c_int32, P]
+    lib.dpd_wait_check.restype = C.c_int
     lib.dpd_batch_create.argtypes = [P, P, P]
     lib.dpd_batch_add.argtypes = [P, P, C.c_int64, P, C.c_int32, P, C.c_double, C.c_double,
                                   C.c_double, P, C.c_int64, P, C.c_int64, C.c_double, C.c_uint64,
@@ -150,6 +152,16 @@ def cells_noalloc(pos_dev_ptr, n, L, key_dev_ptr, order_dev_ptr, cell_start_dev_
     return lib.dpd_cells_noalloc(C.c_void_p(pos_dev_ptr), int(n), C.byref(box),
                                  C.c_void_p(key_dev_ptr), C.c_void_p(order_dev_ptr),
                                  C.c_void_p(cell_start_dev_ptr), C.c_void_p(stream_ptr))
+
+
+WAIT_CHECK_MAX_TRIES = 1 << 22
+
+
+def wait_check(deliver, tries=4096, stream_ptr=None):
+    """dpd_wait_check: one bounded mbarrier wait whose bytes are delivered
+    (deliver=True, DPD_OK) or never delivered (deliver=False: the wait gives up
+    after `tries` polls, DPD_ETIMEOUT).  Returns the DPD_* code."""
+    return lib.dpd_wait_check(1 if deliver else 0, int(tries), C.c_void_p(stream_ptr))
 
 
 def default_options(**kw) -> dpd_options:

@@ -63,3 +63,9 @@ def test_create_rejects_bad_arguments(binding, case):
     with pytest.raises(binding.DPDError) as e:
         binding.System(L, types, a, 4.5, 1.0, dt, bonds=bonds)
     assert e.value.code == binding.DPD_EINVAL
+
+
+def test_wait_check_rejects_bad_arguments(binding):
+    # argument checks come before any CUDA call
+    assert binding.wait_check(True, tries=0) == binding.DPD_EINVAL
+    assert binding.wait_check(True, tries=binding.WAIT_CHECK_MAX_TRIES + 1) == binding.DPD_EINVAL
