@@ -89,7 +89,7 @@ typedef struct {
     int32_t sample_every; /* accumulate running means every k steps (0=off)  */
     int32_t tile_cells;   /* pair-kernel home cells per block (0 = auto)     */
     int32_t threads;      /* pair-kernel threads per block (0 = auto)        */
-    int32_t use_graph;    /* replay steps from a captured CUDA graph (1)     */
+    int32_t use_graph;    /* replay steps from captured CUDA graphs (0)      */
     void *cuda_stream;    /* cudaStream_t to run on; NULL = own stream       */
 } dpd_options;
 
@@ -112,7 +112,10 @@ typedef struct {
 } dpd_obs;
 
 /* Fill *opt with the defaults (lambda 0.65, seed 0, FP32, Gaussian noise,
- * sample_every 0, automatic tiles, graphs on, own stream). */
+ * sample_every 0, automatic tiles, direct launches, own stream).  Direct
+ * launches use programmatic dependent launch, so each kernel of a step is
+ * scheduled while the previous one drains; replaying captured CUDA graphs
+ * (use_graph = 1) gives the same bits. */
 void dpd_default_options(dpd_options *opt);
 
 /* Create a system (eq. 3-8 parameters).  types[n] in [0, ntypes);
@@ -228,7 +231,7 @@ int dpd_wait_check(int32_t deliver, int32_t tries, void *cuda_stream);
  * state) and removed at any time between steps; dpd_batch_step advances
  * every resident system by the same number of steps, each with its own box,
  * parameters, seed and step counter, in one launch per kernel of Fig. 1's
- * loop for all of them (CUDA-graph replayed).  A system draws the same noise
+ * loop for all of them.  A system draws the same noise
  * and follows the same arithmetic alone or in a batch: per-bead sums are in
  * a fixed order and ids, cell keys and Philox counters are its own.
  * Memory admission: dpd_batch_add fails with DPD_ENOMEM when the system's

@@ -149,7 +149,7 @@ void dpd_default_options(dpd_options *opt) {
     opt->sample_every = 0;
     opt->tile_cells = 0;
     opt->threads = 0;
-    opt->use_graph = 1;
+    opt->use_graph = 0;
     opt->cuda_stream = nullptr;
 }
 

@@ -30,6 +30,27 @@ static __global__ void k_fill_int(int *p, int n, int v) {
     if (i < n) p[i] = v;
 }
 
+
+// Launch with programmatic stream serialization: the kernel may be scheduled
+// while the previous kernel of the stream drains, and it waits (griddep_wait,
+// its first statement) until that kernel has completed before it touches
+// memory.  Used for the kernels of a step, which follow one another.
+template <class... KA, class... AA>
+static cudaError_t launch_pdl(void (*k)(KA...), int grid, int block, size_t smem, cudaStream_t st,
+                              AA &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<AA>(args)...);
+}
+
 template <class P>
 class BatchEngine : public BatchBase {
     using real = typename P::real;
@@ -720,7 +741,7 @@ class BatchEngine : public BatchBase {
 
     template <int T, bool S>
     int launch_pair_t(const PairLaunch<P> &pl, int nbr) {
-        k_pair<P, T, S><<<nbr, T, S ? smem_ : smem_n_, stream_>>>(pl);
+        DPD_CU(launch_pdl(k_pair<P, T, S>, nbr, T, S ? smem_ : smem_n_, stream_, pl));
         ++launches_;
         DPD_CU(cudaGetLastError());
         return DPD_OK;
@@ -758,9 +779,9 @@ class BatchEngine : public BatchBase {
     // `old` velocity/force/id buffers into the `nxt` ones
     int enqueue_sort(int b_lo, int b_hi, int c_lo, int c_hi, int old, int nxt) {
         const int C = c_hi - c_lo, nb = (C + SCAN_B - 1) / SCAN_B;
-        k_scan1<<<nb, SCAN_T, 0, stream_>>>(count_ + c_lo, C, bsum_);
-        k_scan3b<<<nb, SCAN_T, 0, stream_>>>(count_ + c_lo, C, bsum_, cell_start_ + c_lo,
-                                             (uint32_t)b_lo);
+        DPD_CU(launch_pdl(k_scan1, nb, SCAN_T, 0, stream_, count_ + c_lo, C, bsum_));
+        DPD_CU(launch_pdl(k_scan3b, nb, SCAN_T, 0, stream_, count_ + c_lo, C,
+                          (const uint32_t *)bsum_, cell_start_ + c_lo, (uint32_t)b_lo));
         ScatterArgs<P> sa;
         sa.b_lo = b_lo;
         sa.b_hi = b_hi;
@@ -772,7 +793,7 @@ class BatchEngine : public BatchBase {
         sa.id_old = id_[old];
         sa.src = src_;
         sa.sid = sid_;
-        k_scatter<P><<<blocks(b_hi - b_lo), 256, 0, stream_>>>(sa);
+        DPD_CU(launch_pdl(k_scatter<P>, blocks(b_hi - b_lo), 256, 0, stream_, sa));
         GatherArgs<P> ga;
         ga.b_lo = b_lo;
         ga.b_hi = b_hi;
@@ -792,7 +813,7 @@ class BatchEngine : public BatchBase {
         ga.key = key_;
         ga.id = id_[nxt];
         ga.inv_perm = used_bonds_ > 0 ? inv_perm_ : nullptr;
-        k_gather<P><<<blocks(b_hi - b_lo), 256, 0, stream_>>>(ga);
+        DPD_CU(launch_pdl(k_gather<P>, blocks(b_hi - b_lo), 256, 0, stream_, ga));
         launches_ += 4;
         DPD_CU(cudaGetLastError());
         return DPD_OK;
@@ -824,13 +845,13 @@ class BatchEngine : public BatchBase {
         ba.status = status_;
         const int g = blocks(b_hi - b_lo);
         if (init) {
-            if (sample) k_bond_vel<P, true, true><<<g, 256, 0, stream_>>>(ba);
-            else k_bond_vel<P, true, false><<<g, 256, 0, stream_>>>(ba);
+            if (sample) DPD_CU(launch_pdl(k_bond_vel<P, true, true>, g, 256, 0, stream_, ba));
+            else DPD_CU(launch_pdl(k_bond_vel<P, true, false>, g, 256, 0, stream_, ba));
         } else if (fuse) {
-            k_bond_vel<P, false, false, true><<<g, 256, 0, stream_>>>(ba);
+            DPD_CU(launch_pdl(k_bond_vel<P, false, false, true>, g, 256, 0, stream_, ba));
         } else {
-            if (sample) k_bond_vel<P, false, true><<<g, 256, 0, stream_>>>(ba);
-            else k_bond_vel<P, false, false><<<g, 256, 0, stream_>>>(ba);
+            if (sample) DPD_CU(launch_pdl(k_bond_vel<P, false, true>, g, 256, 0, stream_, ba));
+            else DPD_CU(launch_pdl(k_bond_vel<P, false, false>, g, 256, 0, stream_, ba));
         }
         ++launches_;
         DPD_CU(cudaGetLastError());
@@ -840,9 +861,11 @@ class BatchEngine : public BatchBase {
     // FP64 observables of systems rsys[k0 .. k0+nk) from chunks [r0, r0+nr)
     int enqueue_reduce(int r0, int nr, int k0, int nk, bool accumulate) {
         if (nr <= 0 || nk <= 0) return DPD_OK;
-        k_reduce<P><<<nr, RED_T, 0, stream_>>>(rmap_ + r0, vel_[cur_], ev_, partial_ + r0 * RED_K);
-        k_reduce_final<P><<<nk, RED_T, 0, stream_>>>(rsys_ + k0, sys_, partial_, obs_, acc_,
-                                                  accumulate ? 1 : 0, status_);
+        DPD_CU(launch_pdl(k_reduce<P>, nr, RED_T, 0, stream_, (const int2 *)(rmap_ + r0),
+                          (const vec4 *)vel_[cur_], (const vec4 *)ev_, partial_ + r0 * RED_K));
+        DPD_CU(launch_pdl(k_reduce_final<P>, nk, RED_T, 0, stream_, (const int4 *)(rsys_ + k0),
+                          (const SysDesc<P> *)sys_, (const double *)partial_, obs_, acc_,
+                          accumulate ? 1 : 0, status_));
         launches_ += 2;
         DPD_CU(cudaGetLastError());
         return DPD_OK;
@@ -870,7 +893,7 @@ class BatchEngine : public BatchBase {
         ua.counter = counter_;
         ua.status = status_;
         if (with_update) {
-            k_update<P><<<blocks(used_beads_), 256, 0, stream_>>>(ua);
+            DPD_CU(launch_pdl(k_update<P>, blocks(used_beads_), 256, 0, stream_, ua));
             ++launches_;
             DPD_CU(cudaGetLastError());
         }

@@ -75,6 +75,14 @@ __device__ __forceinline__ V mk4(R x, R y, R z, R w) {
     return v;
 }
 
+// Programmatic dependent launch: wait until the preceding kernel in the
+// stream has completed and its writes are visible (returns at once when the
+// kernel was launched without the attribute).  The first statement of every
+// kernel of a step.
+__device__ __forceinline__ void griddep_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // Device status bits (sticky until the handle is destroyed).
 enum : int { ST_NONFINITE = 1, ST_TIMEOUT = 2, ST_BADINPUT = 4 };
 
@@ -295,6 +303,7 @@ struct UpdArgs {
 
 template <class P>
 __global__ void __launch_bounds__(256) k_update(UpdArgs<P> a) {
+    griddep_wait();
     const int t = a.b_lo + blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= a.b_hi) return;
     const int s = a.bsys[t];
@@ -383,6 +392,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *total)
 
 static __global__ void __launch_bounds__(SCAN_T) k_scan1(const uint32_t *count, int ncell,
                                                   uint32_t *bsum) {
+    griddep_wait();
     const int base = blockIdx.x * SCAN_B + threadIdx.x * SCAN_V;
     uint32_t s = 0;
 #pragma unroll
@@ -416,6 +426,7 @@ static __global__ void __launch_bounds__(SCAN_T) k_scan2(uint32_t *bsum, int nb,
 static __global__ void __launch_bounds__(SCAN_T) k_scan3b(uint32_t *count, int ncell,
                                                    const uint32_t *bsum, uint32_t *cell_start,
                                                    uint32_t base) {
+    griddep_wait();
     __shared__ uint32_t tot;
     uint32_t before = 0;
     for (int j = threadIdx.x; j < (int)blockIdx.x; j += SCAN_T) before += bsum[j];
@@ -454,6 +465,7 @@ struct ScatterArgs {
 
 template <class P>
 __global__ void __launch_bounds__(256) k_scatter(ScatterArgs<P> a) {
+    griddep_wait();
     const int t = a.b_lo + blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= a.b_hi) return;
     const int s = a.bsys[t];
@@ -482,6 +494,7 @@ struct GatherArgs {
 // with a smaller id (cells hold ~3 beads), and moves its state there.
 template <class P>
 __global__ void __launch_bounds__(256) k_gather(GatherArgs<P> a) {
+    griddep_wait();
     const int t = a.b_lo + blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= a.b_hi) return;
     const SysDesc<P> &D = a.sys[a.bsys[t]];
@@ -671,6 +684,7 @@ __device__ __forceinline__ double theta_pair(uint2 x, int noise, double) {
 
 template <class P, int T, bool SAMPLE>
 __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) k_pair(PairLaunch<P> la) {
+    griddep_wait();
     using real = typename P::real;
     using vec4 = typename P::vec4;
     constexpr int NW = T / 32;
@@ -1130,6 +1144,7 @@ __device__ __forceinline__ void bond_disp(const BondArgs<P> &a, const SysDesc<P>
 
 template <class P, bool INIT, bool SAMPLE, bool FUSE = false>
 __global__ void __launch_bounds__(256) k_bond_vel(BondArgs<P> a) {
+    griddep_wait();
     static_assert(!FUSE || !INIT, "the fused update follows a velocity update");
     using real = typename P::real;
     using vec4 = typename P::vec4;
@@ -1192,6 +1207,7 @@ constexpr int RED_T = 256, RED_CHUNK = 4096, RED_K = 8;
 template <class P>
 __global__ void __launch_bounds__(RED_T) k_reduce(const int2 *rmap, const typename P::vec4 *vel,
                                                   const typename P::vec4 *ev, double *partial) {
+    griddep_wait();
     const int2 r = rmap[blockIdx.x];
     double s[RED_K] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int t = r.x + threadIdx.x; t < r.y; t += RED_T) {
@@ -1225,6 +1241,7 @@ template <class P>
 __global__ void __launch_bounds__(RED_T)
     k_reduce_final(const int4 *rsys, const SysDesc<P> *sys, const double *partial, double *obs,
                    double *acc, int accumulate, int *status) {
+    griddep_wait();
     const int4 q = rsys[blockIdx.x];
     const int s = q.x;
     // every thread sums a strided share of the system's block partials, then

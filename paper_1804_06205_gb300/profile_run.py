@@ -17,13 +17,13 @@ def main():
     ap.add_argument("--steps", type=int, default=6)
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
-    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--graph", action="store_true")
     args = ap.parse_args()
     from . import dpd as D
     from . import workloads as W
     w = W.make(args.workload)
     g = D.System.from_workload(w, precision=args.precision, threads=args.threads,
-                               use_graph=0 if args.no_graph else 1)
+                               use_graph=1 if args.graph else 0)
     g.set_state(w.pos, w.vel, 0)
     g.sync()
     t0 = time.perf_counter()

@@ -55,9 +55,9 @@ def tile_for(table: Optional[dict], L) -> int:
 class Server:
     """precision 0 = FP32 path, 1 = FP64 path; table = autotuner output;
     use_graph: replay each step shape as a CUDA graph or launch the kernels
-    directly (the default: admissions and departures come every few chunks
-    and each would force the graphs to be captured again, which costs more
-    than the launches they save)."""
+    directly (the default: direct launches overlap each kernel's start with
+    the previous kernel's end through programmatic dependent launch, and
+    admissions and departures would force the graphs to be captured again)."""
 
     def __init__(self, max_beads=2_000_000, max_cells=2_000_000, max_bonds=1_000_000,
                  max_systems=128, chunk=50, precision=0, table=None, keep_states=False,

@@ -37,7 +37,7 @@ def test_strerror_and_defaults(binding):
     assert binding.strerror(binding.DPD_EUNSTABLE).startswith("non-finite")
     o = binding.default_options()
     assert abs(o.lambda_ - 0.65) < 1e-15 and o.precision == binding.DPD_FP32
-    assert o.use_graph == 1 and o.cuda_stream is None
+    assert o.use_graph == 0 and o.cuda_stream is None
 
 
 @pytest.mark.parametrize("case", ["small_box", "asym_a", "bad_type", "bad_bond", "dt0",

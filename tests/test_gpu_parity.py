@@ -240,7 +240,7 @@ def test_graph_replay_is_bitwise_and_tilings_agree(D):
     (tile cells, threads) change only the summation tree of each bead's force."""
     w = WL["odd_box"]
     outs = {}
-    for name, opt in (("graph", dict()), ("direct", dict(use_graph=0)),
+    for name, opt in (("graph", dict(use_graph=1)), ("direct", dict()),
                       ("t64", dict(tile_cells=3, threads=64)),
                       ("t256", dict(tile_cells=12, threads=256)),
                       ("t128x1", dict(tile_cells=1, threads=128, use_graph=0))):
