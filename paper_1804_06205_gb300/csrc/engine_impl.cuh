@@ -64,6 +64,7 @@ class BatchEngine : public BatchBase {
         int X = 1, BY = 1, BZ = 1, nbx = 1, nby = 1, nbz = 1, cap = 64;
         int64_t step = 0;
         int red0 = 0, nred = 0, rsys_index = 0;   // reduction chunks, entry in rsys
+        bool obs_fresh = false;   // obs_ holds the observables of the current state
     };
 
     struct GraphSlot {
@@ -286,10 +287,10 @@ class BatchEngine : public BatchBase {
         DPD_CU(cudaMemcpyAsync(counter_ + s, &sv, sizeof(long long), cudaMemcpyHostToDevice,
                                stream_));
         if ((rc = enqueue_sort(h.bead0, h.bead0 + h.n, h.cell0, h.cell0 + h.ncell, old, cur_)) ||
-            (rc = launch_pair(true, h.brick0, h.nbrick)) ||
-            (rc = enqueue_bonds(true, true, h.bead0, h.bead0 + h.n)) ||
-            (rc = enqueue_reduce(h.red0, h.nred, h.rsys_index, 1, false)))
+            (rc = launch_pair(false, h.brick0, h.nbrick)) ||
+            (rc = enqueue_bonds(true, false, h.bead0, h.bead0 + h.n)))
             return rc;
+        h.obs_fresh = false;
         DPD_CU(cudaStreamSynchronize(stream_));
         int st = 0;
         DPD_CU(cudaMemcpy(&st, status_, sizeof(int), cudaMemcpyDeviceToHost));
@@ -312,21 +313,26 @@ class BatchEngine : public BatchBase {
             if (!hs_[k].has_state) return DPD_ENOSTATE;
         int rc = peek_status();
         if (rc) return rc;
-        // A plain step is never the last of a call: its bond kernel also does the
-        // next step's position update, which that step then skips.
-        bool updated = false;
+        // Step kinds: 0 plain, its bond kernel also doing the next step's position
+        // update (which that step then skips); 1 plain without it, the last step of
+        // a call; 2 sampled for the running means.  Observables are otherwise
+        // computed on demand from the state (observables()).
+        bool updated = false, sampled = false;
         for (int64_t k = 0; k < nsteps; ++k) {
             // running means: one system's steps decide when (a batch of one)
             const bool acc = bc_.sample_every > 0 && order_.size() == 1 &&
                              ((hs_[order_[0]].step + 1) % bc_.sample_every) == 0;
-            const bool sample = acc || (k == nsteps - 1);
-            const int variant = (acc ? 2 : (sample ? 1 : 0)) + (updated ? 3 : 0);
+            const int base = acc ? 2 : (k == nsteps - 1 ? 1 : 0);
+            const int variant = base + (updated ? 3 : 0);
             rc = bc_.use_graph ? launch_graph(variant)
-                               : enqueue_step(sample, acc, false, !updated, !sample);
+                               : enqueue_step(acc, acc, false, !updated, base == 0);
             if (rc) return rc;
-            updated = !sample;
+            updated = base == 0;
+            sampled = acc;
             for (int s : order_) hs_[s].step += 1;
         }
+        if (nsteps > 0)
+            for (int s : order_) hs_[s].obs_fresh = sampled;
         return DPD_OK;
     }
 
@@ -373,6 +379,16 @@ class BatchEngine : public BatchBase {
         if (s < 0 || s >= NS_ || !hs_[s].live) return DPD_EINVAL;
         SysHost &h = hs_[s];
         if (!h.has_state) return DPD_ENOSTATE;
+        if (!h.obs_fresh) {   // the sampled pair sums and the bond sums of this state
+            int rc = check_status();
+            if (rc) return rc;
+            if ((rc = launch_pair(true, h.brick0, h.nbrick)) ||
+                (h.nbond > 0 && (rc = enqueue_bonds(false, false, h.bead0, h.bead0 + h.n,
+                                                    false, true))) ||
+                (rc = enqueue_reduce(h.red0, h.nred, h.rsys_index, 1, false)))
+                return rc;
+            h.obs_fresh = true;
+        }
         double o[RED_K], acc[4];
         DPD_CU(cudaMemcpyAsync(o, obs_ + (size_t)s * RED_K, sizeof(o), cudaMemcpyDeviceToHost,
                                stream_));
@@ -820,7 +836,8 @@ class BatchEngine : public BatchBase {
     }
 
     // bonds (+ velocity update unless init) over beads [b_lo, b_hi)
-    int enqueue_bonds(bool init, bool sample, int b_lo, int b_hi, bool fuse = false) {
+    int enqueue_bonds(bool init, bool sample, int b_lo, int b_hi, bool fuse = false,
+                      bool obs_only = false) {
         BondArgs<P> ba;
         ba.b_lo = b_lo;
         ba.b_hi = b_hi;
@@ -844,7 +861,9 @@ class BatchEngine : public BatchBase {
         ba.counter = counter_;
         ba.status = status_;
         const int g = blocks(b_hi - b_lo);
-        if (init) {
+        if (obs_only) {
+            DPD_CU(launch_pdl(k_bond_obs<P>, g, 256, 0, stream_, ba));
+        } else if (init) {
             if (sample) DPD_CU(launch_pdl(k_bond_vel<P, true, true>, g, 256, 0, stream_, ba));
             else DPD_CU(launch_pdl(k_bond_vel<P, true, false>, g, 256, 0, stream_, ba));
         } else if (fuse) {
@@ -968,7 +987,7 @@ class BatchEngine : public BatchBase {
             cudaGraph_t graph = nullptr;
             DPD_CU(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal));
             const int base = variant % 3;
-            int rc = enqueue_step(base >= 1, base == 2, true, variant < 3, base == 0);
+            int rc = enqueue_step(base == 2, base == 2, true, variant < 3, base == 0);
             cudaError_t e = cudaStreamEndCapture(stream_, &graph);
             cur_ = cur0;   // capture did not execute anything
             if (rc) {
@@ -1049,7 +1068,7 @@ class BatchEngine : public BatchBase {
     int cur_ = 0;
     int64_t launches_ = 0;
     int status_host_ = 0;
-    GraphSlot graphs_[2][6];   // [parity][variant]: plain/sampled/accumulating x with/without update
+    GraphSlot graphs_[2][6];   // [parity][variant]: fused/last/accumulating x with/without update
     cudaEvent_t ph_[4] = {nullptr, nullptr, nullptr, nullptr};
     std::vector<cudaEvent_t> prof_ev_;
     int64_t prof_max_ = 0, prof_n_ = 0;

@@ -1069,26 +1069,30 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
 template <class R>
 __device__ __forceinline__ void bond_force(int kind, R r0, R k, R alpha, R dx, R dy, R dz, R &fx,
                                            R &fy, R &fz, R &U) {
-    const R r2 = dx * dx + dy * dy + dz * dz;
+    // explicit rounding throughout: every kernel that calls this gets the same bits
+    const R r2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
     const R r = sqrt(r2);
     R coef = 0;
     U = 0;
     if (kind == 1) {
         if (r0 == (R)0) {
             coef = -k;
-            U = (R)0.5 * k * r2;
+            U = mul_rn(mul_rn((R)0.5, k), r2);
         } else {
-            U = (R)0.5 * k * (r - r0) * (r - r0);
-            if (r > (R)0) coef = -k * (r - r0) / r;
+            const R d = r - r0;
+            U = mul_rn(mul_rn((R)0.5, k), mul_rn(d, d));
+            if (r > (R)0) coef = mul_rn(-k, d) / r;
         }
     } else if (kind == 2) {
-        const R e = exp(-alpha * fabs(r - r0));
-        U = k * ((R)1 - e) * ((R)1 - e);
-        if (r > (R)0) coef = -(R)2 * k * alpha * e * ((R)1 - e) / r;
+        const R e = exp(mul_rn(-alpha, fabs(r - r0)));
+        const R om = (R)1 - e;
+        U = mul_rn(mul_rn(k, om), om);
+        if (r > (R)0) coef = mul_rn(mul_rn(mul_rn((R)-2 * k, alpha), e), om) / r;
     } else if (kind == 3) {
-        const R x = exp(-alpha * (r - r0));
-        U = k * (((R)1 - x) * ((R)1 - x) - (R)1);
-        if (r > (R)0) coef = -(R)2 * k * alpha * x * ((R)1 - x) / r;
+        const R x = exp(mul_rn(-alpha, r - r0));
+        const R om = (R)1 - x;
+        U = mul_rn(k, mul_rn(om, om) - (R)1);
+        if (r > (R)0) coef = mul_rn(mul_rn(mul_rn((R)-2 * k, alpha), x), om) / r;
     }
     fx = mul_rn(coef, dx);
     fy = mul_rn(coef, dy);
@@ -1165,12 +1169,12 @@ __global__ void __launch_bounds__(256) k_bond_vel(BondArgs<P> a) {
         fx = add_rn(fx, gx);
         fy = add_rn(fy, gy);
         fz = add_rn(fz, gz);
-        if (SAMPLE) {
-            wb += dx * gx + dy * gy + dz * gz;
-            eb += U;
+        if (SAMPLE) {   // rounded as in k_bond_obs, so both give the same bits
+            wb = add_rn(wb, fma_rn(dz, gz, fma_rn(dy, gy, mul_rn(dx, gx))));
+            eb = add_rn(eb, U);
         }
     }
-    vec4 vn;
+    vec4 vn = mk4<vec4, real>((real)0, (real)0, (real)0, (real)0);
     if (!INIT) {
         const real hdt = D.half_dt;
         const vec4 v = a.vel[t], f = a.frc[t];
@@ -1180,6 +1184,9 @@ __global__ void __launch_bounds__(256) k_bond_vel(BondArgs<P> a) {
     }
     const vec4 fn = mk4<vec4, real>(fx, fy, fz, (real)0);
     a.frc[t] = fn;
+    if (!FUSE) {   // (the fused update checks the positions it makes)
+        if (!isfinite(fx + fy + fz + vn.x + vn.y + vn.z)) atomicOr(a.status, ST_NONFINITE);
+    }
     if (FUSE) {   // Fig. 1 steps 1-2 of the next step, from this step's v and f
         if (t == D.bead0) a.counter[sysi] += 1;
         vec4 out;
@@ -1193,6 +1200,33 @@ __global__ void __launch_bounds__(256) k_bond_vel(BondArgs<P> a) {
         const vec4 e = a.ev[t];
         a.ev[t] = mk4<vec4, real>(e.x, e.y, wb, eb);
     }
+}
+
+// Bond virial and energy of every bead's bond records (ev.z, ev.w), from the
+// current positions and nothing else written: the bond half of an observables
+// pass made on demand, with the rounded accumulation of the sampled k_bond_vel.
+template <class P>
+__global__ void __launch_bounds__(256) k_bond_obs(BondArgs<P> a) {
+    griddep_wait();
+    using real = typename P::real;
+    using vec4 = typename P::vec4;
+    const int t = a.b_lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.b_hi) return;
+    const SysDesc<P> &D = a.sys[a.bsys[t]];
+    real wb = 0, eb = 0;
+    const int32_t i = a.id[t];
+    const int b0 = a.bptr[D.bead0 + i], b1 = a.bptr[D.bead0 + i + 1];
+    for (int b = b0; b < b1; ++b) {
+        const int u = a.inv_perm[D.bead0 + a.bpartner[b]];
+        const vec4 bp = a.bpar[b];
+        real dx, dy, dz, gx, gy, gz, U;
+        bond_disp<P>(a, D, t, u, dx, dy, dz);
+        bond_force<real>((int)bp.w, bp.x, bp.y, bp.z, dx, dy, dz, gx, gy, gz, U);
+        wb = add_rn(wb, fma_rn(dz, gz, fma_rn(dy, gy, mul_rn(dx, gx))));
+        eb = add_rn(eb, U);
+    }
+    const vec4 e = a.ev[t];
+    a.ev[t] = mk4<vec4, real>(e.x, e.y, wb, eb);
 }
 
 // --------------------------------------------------------------------------

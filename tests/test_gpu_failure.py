@@ -37,3 +37,20 @@ def test_undelivered_wait_gives_up_and_context_survives(D):
     g.close()
     assert step == 5 and np.isfinite(pos).all() and np.isfinite(vel).all()
 
+
+def test_force_overflow_is_reported_as_unstable(D):
+    """A repulsion so strong that binary32 forces overflow: the force
+    evaluation of set_state flags it and the call reports DPD_EUNSTABLE;
+    cell indices stay in range for any value, so nothing else is affected."""
+    w = W.fluid(6.0, a_same=3.0e38, seed=5)
+    g = D.System.from_workload(w, precision=D.DPD_FP32)
+    with pytest.raises(D.DPDError) as e:
+        g.set_state(w.pos, w.vel, 0)
+    assert e.value.code == D.DPD_EUNSTABLE
+    g.close()
+    w = W.fluid_3k()
+    g = D.System.from_workload(w, precision=D.DPD_FP32)
+    g.set_state(w.pos, w.vel, 0)
+    g.step(3)
+    assert np.isfinite(g.get_state()[2]).all()
+    g.close()

@@ -218,6 +218,28 @@ def test_observables_match_oracle_at_identical_state(D, prec):
     assert o["step"] == 5
 
 
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_observables_on_demand_equal_in_step_sampling(D, prec):
+    """Observables are computed when asked for, from the state; sampling every
+    step inside the step loop (running means) reaches the same state with the
+    same bits and reports the same instantaneous observables, bit for bit."""
+    w = WL["peptide"]
+    out = []
+    for every in (0, 1):
+        g = gsys(D, w, prec, sample_every=every)
+        g.set_state(w.pos, w.vel, 0)
+        g.step(6)
+        pos, vel, f, _ = g.get_state()
+        out.append((pos, vel, f, g.observables()))
+        g.close()
+    for a, b in zip(out[0][:3], out[1][:3]):
+        assert np.array_equal(a, b)
+    o0, o1 = out[0][3], out[1][3]
+    assert o1["n_samples"] == 6 and o0["n_samples"] == 0
+    for k in ("kT", "p_total", "p_cons", "p_bond", "e_pair", "e_bond"):
+        assert o0[k] == o1[k], (k, o0[k], o1[k])
+
+
 # ------------------------------------------------------------------ invariants
 @pytest.mark.parametrize("prec", [FP32, FP64])
 def test_momentum_conserved_and_runs_deterministic(D, prec):
