@@ -63,14 +63,14 @@ PAIR_OPS_PER_BEAD = 40.5 * 7 + 6.28 * 103
 # the cell count (60 B), plus the bond table pointers: ~144 B.
 SORT_BYTES_PER_BEAD = 172.0
 # DRAM bytes (read + written) per bead of one k_pair launch, from an ncu
-# capture of the current pair kernel on the 70^3 fluid (dram__bytes_read.sum +
-# dram__bytes_write.sum = 39.39 MB for 1,029,000 beads); the launch's force
-# writes stay in L2 and reach DRAM in later kernels.
-PAIR_DRAM_BYTES_PER_BEAD = 38.28
+# capture of the current pair kernel on this workload (dram__bytes_read.sum +
+# dram__bytes_write.sum = 143.7 MB for 3,000,000 beads; the algorithmic
+# minimum is 48 B per bead).
+PAIR_DRAM_BYTES_PER_BEAD = 47.91
 # Thread instructions executed per bead by one k_pair launch, from the same
 # capture (smsp__inst_executed.sum x thread_inst_executed_per_inst_executed):
 # the issued work, against which the issue-rate roofline is taken.
-PAIR_THREAD_INST_PER_BEAD = 4911.0
+PAIR_THREAD_INST_PER_BEAD = 4631.0
 BOND_BYTES_PER_BEAD = 144.0
 
 
@@ -426,7 +426,7 @@ def main():
     roofline = {"bound": "alu", "kernel": "k_pair", "achieved": achieved / 1e12,
                 "peak": alu_peak / 1e12, "unit": "Tops/s", "frac": achieved / alu_peak,
                 "traffic": PAIR_DRAM_BYTES_PER_BEAD * w.n,
-                "traffic_note": "bytes per launch, ncu dram read+write scaled by bead count",
+                "traffic_note": "bytes per launch: ncu dram read+write of one launch on this workload",
                 "ops_per_bead": PAIR_OPS_PER_BEAD, "launch_ms": pair_ms,
                 "issued": {"thread_inst_per_bead": PAIR_THREAD_INST_PER_BEAD,
                            "achieved": PAIR_THREAD_INST_PER_BEAD * w.n / (pair_ms * 1e-3) / 1e12,
