@@ -590,6 +590,7 @@ struct PairSmem {
         using real = typename P::real;
         using vec4 = typename P::vec4;
         size_t b = 2 * (size_t)cap * sizeof(vec4);                 // staged positions, v~
+        if (!P::kOffsets) b += (size_t)cap * sizeof(float4);      // FP64: their binary32 copies
         b += 2 * PAIR_NR * (size_t)(X + 3) * sizeof(int);          // staged / source cell starts
         b += PAIR_NR * 3 * PAIR_PC * sizeof(int) + 4 * 4 * sizeof(int);   // runs, home rows
         b = align16(b);
@@ -726,7 +727,9 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
     const int X = a.X;
     vec4 *s_pos = reinterpret_cast<vec4 *>(smem);
     vec4 *s_vt = s_pos + cap;
-    int *s_cs = reinterpret_cast<int *>(s_vt + cap);
+    // FP64 path: binary32 copies of the staged frame positions, for the scan
+    float4 *s_p32 = reinterpret_cast<float4 *>(s_vt + cap);
+    int *s_cs = reinterpret_cast<int *>(s_p32 + (P::kOffsets ? 0 : cap));
     int *s_src = s_cs + PAIR_NR * (la.Xmax + 3);
     int *s_pc = s_src + PAIR_NR * (la.Xmax + 3);
     int *s_hr = s_pc + PAIR_NR * 3 * PAIR_PC;        // home rows: staged row, first, count, global
@@ -903,6 +906,8 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
                 p.y = add_rn(p.y, sy);
                 p.z = add_rn(p.z, sz);
                 s_pos[q - c0] = p;
+                if (!P::kOffsets)
+                    s_p32[q - c0] = make_float4((float)p.x, (float)p.y, (float)p.z, 0.0f);
             }
         }
         __syncthreads();   // staged and moved before anyone scans
@@ -946,11 +951,19 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
             }
         }
         real ax = 0, ay = 0, az = 0, aw = 0, ae = 0;   // this bead's sums
-        // distances from the bead to the faces of its cell (pruning)
-        const real lxd = hp.x - (real)uxi * hx, uxd = hx - lxd;
-        const real lyd = hp.y - (real)ry * hy, uyd = hy - lyd;
-        const real lzd = hp.z - (real)rz * hz, uzd = hz - lzd;
-        const real cut2 = (real)1.0001;
+        // distances from the bead to the faces of its cell (pruning); the scan
+        // runs in binary32 on both paths (FP64: on binary32 copies of the
+        // positions, with margins far above their rounding)
+        const float lxd = (float)(hp.x - (real)uxi * hx), uxd = (float)hx - lxd;
+        const float lyd = (float)(hp.y - (real)ry * hy), uyd = (float)hy - lyd;
+        const float lzd = (float)(hp.z - (real)rz * hz), uzd = (float)hz - lzd;
+        const float cut2 = 1.0001f;
+        // FP32: a hit is 0 < r^2 < 1 (the bead's staged copy coincides with it);
+        // FP64: r^2 < 1.001 in binary32 and not the bead itself, and the exact
+        // test is made in the evaluation, so the hits summed are the same
+        constexpr float scan_lim = P::kOffsets ? 1.0f : 1.001f;
+        const float4 *s_scan = P::kOffsets ? reinterpret_cast<const float4 *>(s_pos) : s_p32;
+        const int self_abs = active ? s_cs[sr_home * W + 1] + (hb - s_hr[4 * hr + 1]) : -1;
 
         for (int c0 = 0; c0 < S; c0 += cap) {
             const int c1 = min(S, c0 + cap);
@@ -960,6 +973,9 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
             }
             __syncwarp();
             const real xi = hp.x, yi = hp.y, zi = hp.z;
+            const float xs = (float)hp.x, ys = (float)hp.y, zs = (float)hp.z;
+            const uint16_t self =
+                (self_abs >= c0 && self_abs < c1) ? (uint16_t)(self_abs - c0) : (uint16_t)0xFFFF;
             int r9 = 0, q = 0;
             bool more = active;
             while (__any_sync(FULL, more)) {
@@ -984,29 +1000,30 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
                             qe = q + PAIR_HMAX;                  // a crowded row: part of it
                         }
                         {   // queue [level][lane]: the staged slot of each hit
-                            const vec4 *pp = s_pos + (q - c0);
+                            const float4 *pp = s_scan + (q - c0);
                             uint16_t ent = (uint16_t)(q - c0);
                             uint16_t *qp = my_q + nh * 32 + lane;
                             for (; q + 1 < qe; q += 2, pp += 2, ent += 2) {   // two at a time
-                                const vec4 pa = pp[0], pb = pp[1];
-                                const real ax = xi - pa.x, ay = yi - pa.y, az = zi - pa.z;
-                                const real bx = xi - pb.x, by = yi - pb.y, bz = zi - pb.z;
-                                const real ra = fma_rn(az, az, fma_rn(ay, ay, mul_rn(ax, ax)));
-                                const real rb = fma_rn(bz, bz, fma_rn(by, by, mul_rn(bx, bx)));
-                                if (ra < (real)1 && ra > (real)0) {
+                                const float4 pa = pp[0], pb = pp[1];
+                                const float ax = xs - pa.x, ay = ys - pa.y, az = zs - pa.z;
+                                const float bx = xs - pb.x, by = ys - pb.y, bz = zs - pb.z;
+                                const float ra = fma_rn(az, az, fma_rn(ay, ay, mul_rn(ax, ax)));
+                                const float rb = fma_rn(bz, bz, fma_rn(by, by, mul_rn(bx, bx)));
+                                if (ra < scan_lim && (P::kOffsets ? ra > 0.0f : ent != self)) {
                                     *qp = ent;
                                     qp += 32;
                                 }
-                                if (rb < (real)1 && rb > (real)0) {
+                                if (rb < scan_lim &&
+                                    (P::kOffsets ? rb > 0.0f : (uint16_t)(ent + 1) != self)) {
                                     *qp = (uint16_t)(ent + 1);
                                     qp += 32;
                                 }
                             }
                             if (q < qe) {
-                                const vec4 pj = *pp;
-                                const real dx = xi - pj.x, dyv = yi - pj.y, dzv = zi - pj.z;
-                                const real r2 = fma_rn(dzv, dzv, fma_rn(dyv, dyv, mul_rn(dx, dx)));
-                                if (r2 < (real)1 && r2 > (real)0) {
+                                const float4 pj = *pp;
+                                const float dx = xs - pj.x, dyv = ys - pj.y, dzv = zs - pj.z;
+                                const float r2 = fma_rn(dzv, dzv, fma_rn(dyv, dyv, mul_rn(dx, dx)));
+                                if (r2 < scan_lim && (P::kOffsets ? r2 > 0.0f : ent != self)) {
                                     *qp = ent;
                                     qp += 32;
                                 }
@@ -1028,6 +1045,7 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
                         const vec4 pj = s_pos[jl], vj = s_vt[jl];
                         const real dx = xi - pj.x, dyv = yi - pj.y, dzv = zi - pj.z;
                         const real r2 = fma_rn(dzv, dzv, fma_rn(dyv, dyv, mul_rn(dx, dx)));
+                        if (!P::kOffsets && !(r2 < (real)1 && r2 > (real)0)) continue;
                         const real rinv = rsqrt_r(r2);
                         const real rr1 = mul_rn(r2, rinv);
                         const real w = (real)1 - rr1;
