@@ -914,6 +914,8 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
         return true;
     };
     int staged_lo = -1;
+    // FP64: balanced evaluation (ranks in s_src, which holds PAIR_NR * (Xmax + 3) ints)
+    const bool balance = !P::kOffsets && PAIR_NR * (la.Xmax + 3) >= T;
 
     for (int hb0 = 0; hb0 < H; hb0 += T) {
         const int hb = hb0 + tid;
@@ -965,6 +967,44 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
         const float4 *s_scan = P::kOffsets ? reinterpret_cast<const float4 *>(s_pos) : s_p32;
         const int self_abs = active ? s_cs[sr_home * W + 1] + (hb - s_hr[4 * hr + 1]) : -1;
 
+        // the queue qb[m * 32 + col], m < n, of the bead at ip (v~ iv): each
+        // lane takes its entries in scan order and adds them to the sums
+        auto evaluate = [&](const uint16_t *qb, int col, int n, const vec4 &ip, const vec4 &iv,
+                            real &sx, real &sy, real &sz, real &sw, real &se) {
+                const int nmax = (int)__reduce_max_sync(FULL, (unsigned)n);
+                for (int m = 0; m < nmax; ++m) {
+                    if (m < n) {
+                        const int jl = qb[m * 32 + col];
+                        const vec4 pj = s_pos[jl], vj = s_vt[jl];
+                        const real dx = ip.x - pj.x, dyv = ip.y - pj.y, dzv = ip.z - pj.z;
+                        const real r2 = fma_rn(dzv, dzv, fma_rn(dyv, dyv, mul_rn(dx, dx)));
+                        if (!P::kOffsets && !(r2 < (real)1 && r2 > (real)0)) continue;
+                        const real rinv = rsqrt_r(r2);
+                        const real rr1 = mul_rn(r2, rinv);
+                        const real w = (real)1 - rr1;
+                        const real ex = mul_rn(dx, rinv), ey = mul_rn(dyv, rinv), ez = mul_rn(dzv, rinv);
+                        const real evel = fma_rn(ez, iv.z - vj.z,
+                                                 fma_rn(ey, iv.y - vj.y, mul_rn(ex, iv.x - vj.x)));
+                        const real aij = s_a[P::unpack_int(ip.w) * nt + P::unpack_int(pj.w)];
+                        const int32_t idi = P::unpack_int(iv.w), idj = P::unpack_int(vj.w);
+                        const uint32_t lo = (uint32_t)min(idi, idj), hi = (uint32_t)max(idi, idj);
+                        const uint2 rnd = philox_rk(lo, hi, s_lo, s_hi, rkl);
+                        const real th = theta_pair(rnd, a.noise, (real)0);
+                        const real fc = mul_rn(aij, w);
+                        const real gw2 = mul_rn(mul_rn(a.gamma, w), w);
+                        const real mag = fma_rn(mul_rn(a.sig_sqdt, w), th, fma_rn(-gw2, evel, fc));
+                        sx = add_rn(sx, mul_rn(mag, ex));
+                        sy = add_rn(sy, mul_rn(mag, ey));
+                        sz = add_rn(sz, mul_rn(mag, ez));
+                        if (SAMPLE) {
+                            sw += rr1 * fc;
+                            se += (real)0.5 * fc * w;
+                        }
+                    }
+                }
+        };
+        bool done = false;   // the forces were written by the balanced evaluation
+
         for (int c0 = 0; c0 < S; c0 += cap) {
             const int c1 = min(S, c0 + cap);
             if (staged_lo != c0) {
@@ -972,21 +1012,19 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
                 staged_lo = c0;
             }
             __syncwarp();
-            const real xi = hp.x, yi = hp.y, zi = hp.z;
             const float xs = (float)hp.x, ys = (float)hp.y, zs = (float)hp.z;
             const uint16_t self =
                 (self_abs >= c0 && self_abs < c1) ? (uint16_t)(self_abs - c0) : (uint16_t)0xFFFF;
             int r9 = 0, q = 0;
             bool more = active;
-            while (__any_sync(FULL, more)) {
-                // ---- scan: up to PAIR_HMAX hits, rows (dz, dy) ascending, slots ascending
-                int nh = 0;
+            // ---- scan: up to PAIR_HMAX hits, rows (dz, dy) ascending, slots ascending
+            auto scan = [&](int &nh) {
                 if (more) {
                     for (; r9 < 9; ++r9) {
                         const int dy = r9 % 3 - 1, dz = r9 / 3 - 1;
-                        const real ey = dy < 0 ? lyd : (dy > 0 ? uyd : (real)0);
-                        const real ez = dz < 0 ? lzd : (dz > 0 ? uzd : (real)0);
-                        const real dyz = ey * ey + ez * ez;
+                        const float ey = dy < 0 ? lyd : (dy > 0 ? uyd : 0.0f);
+                        const float ez = dz < 0 ? lzd : (dz > 0 ? uzd : 0.0f);
+                        const float dyz = ey * ey + ez * ez;
                         if (dyz >= cut2) continue;                       // row out of reach
                         const int sr = sr_home + dy + SY * dz;
                         const int* cs = s_cs + sr * W + uxi;
@@ -1035,44 +1073,75 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
                     }
                     more = r9 < 9;
                 }
+            };
+            if (balance && S <= cap) {
+                // FP64, one chunk: the first pass of every lane in the block, then,
+                // if no lane needs another, thread t evaluates the queue of the bead
+                // of rank t by hit count (most first), so that a warp's queues have
+                // similar lengths: lanes left idle by short queues still occupy the
+                // FP64 pipe.  Each bead's terms are added in scan order as before.
+                if (tid <= PAIR_HMAX) s_pc[tid] = 0;     // histogram of hit counts
+                int nh = 0;
+                scan(nh);
                 __syncwarp();
-                // ---- evaluate: each lane takes its own hits in scan order and adds
-                // them to its bead's sums in registers
-                const int nmax = (int)__reduce_max_sync(FULL, (unsigned)nh);
-                for (int m = 0; m < nmax; ++m) {
-                    if (m < nh) {
-                        const int jl = my_q[m * 32 + lane];
-                        const vec4 pj = s_pos[jl], vj = s_vt[jl];
-                        const real dx = xi - pj.x, dyv = yi - pj.y, dzv = zi - pj.z;
-                        const real r2 = fma_rn(dzv, dzv, fma_rn(dyv, dyv, mul_rn(dx, dx)));
-                        if (!P::kOffsets && !(r2 < (real)1 && r2 > (real)0)) continue;
-                        const real rinv = rsqrt_r(r2);
-                        const real rr1 = mul_rn(r2, rinv);
-                        const real w = (real)1 - rr1;
-                        const real ex = mul_rn(dx, rinv), ey = mul_rn(dyv, rinv), ez = mul_rn(dzv, rinv);
-                        const real evel = fma_rn(ez, hv.z - vj.z,
-                                                 fma_rn(ey, hv.y - vj.y, mul_rn(ex, hv.x - vj.x)));
-                        const real aij = s_a[P::unpack_int(hp.w) * nt + P::unpack_int(pj.w)];
-                        const int32_t idi = P::unpack_int(hv.w), idj = P::unpack_int(vj.w);
-                        const uint32_t lo = (uint32_t)min(idi, idj), hi = (uint32_t)max(idi, idj);
-                        const uint2 rnd = philox_rk(lo, hi, s_lo, s_hi, rkl);
-                        const real th = theta_pair(rnd, a.noise, (real)0);
-                        const real fc = mul_rn(aij, w);
-                        const real gw2 = mul_rn(mul_rn(a.gamma, w), w);
-                        const real mag = fma_rn(mul_rn(a.sig_sqdt, w), th, fma_rn(-gw2, evel, fc));
-                        ax = add_rn(ax, mul_rn(mag, ex));
-                        ay = add_rn(ay, mul_rn(mag, ey));
-                        az = add_rn(az, mul_rn(mag, ez));
-                        if (SAMPLE) {
-                            aw += rr1 * fc;
-                            ae += (real)0.5 * fc * w;
+                if (!__syncthreads_or(more)) {
+                    if (active) atomicAdd(&s_pc[PAIR_HMAX - nh], 1);
+                    __syncthreads();
+                    if (tid < 32) {   // bin starts, most hits first
+                        const int v = s_pc[tid];
+                        int inc = v;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int u = __shfl_up_sync(FULL, inc, o);
+                            if (tid >= o) inc += u;
                         }
+                        s_pc[tid] = inc - v;
+                        if (tid == 31) s_pc[32] = inc;
                     }
+                    __syncthreads();
+                    if (active) s_src[atomicAdd(&s_pc[PAIR_HMAX - nh], 1)] = tid | (nh << 8);
+                    __syncthreads();
+                    const int nact = min(T, H - hb0);
+                    int own = 0, on = 0, go = 0;
+                    vec4 ip = hp, iv = hv;
+                    if (tid < nact) {   // the bead of rank tid: its staged copy is its state
+                        const int v = s_src[tid];
+                        own = v & 255;
+                        on = v >> 8;
+                        const int ob = hb0 + own;
+                        int orow = 0;
+                        while (orow < 3 && ob >= s_hr[4 * (orow + 1) + 1]) ++orow;
+                        const int k = ob - s_hr[4 * orow + 1];
+                        go = s_hr[4 * orow + 3] + k;
+                        const int oself = s_cs[s_hr[4 * orow] * W + 1] + k;
+                        ip = s_pos[oself];
+                        iv = s_vt[oself];
+                    }
+                    real bx = 0, by = 0, bz = 0, bw = 0, be = 0;
+                    evaluate(s_q + (own >> 5) * PAIR_HMAX * 32, own & 31, on, ip, iv, bx, by, bz,
+                             bw, be);
+                    __syncwarp();
+                    if (tid < nact) {
+                        a.fpair[go] = mk4<vec4, real>(bx, by, bz, (real)0);
+                        if (SAMPLE) a.ev[go] = mk4<vec4, real>(bw, be, (real)0, (real)0);
+                    }
+                    done = true;
+                    __syncthreads();   // every queue read before the next scan
+                    break;
                 }
+                // some lane needs another pass: evaluate this one, then go on as usual
+                evaluate(my_q, lane, nh, hp, hv, ax, ay, az, aw, ae);
+                __syncwarp();
+            }
+            while (__any_sync(FULL, more)) {
+                int nh = 0;
+                scan(nh);
+                __syncwarp();
+                evaluate(my_q, lane, nh, hp, hv, ax, ay, az, aw, ae);
                 __syncwarp();
             }
         }
-        if (active) {
+        if (active && !done) {
             a.fpair[g] = mk4<vec4, real>(ax, ay, az, (real)0);
             if (SAMPLE) a.ev[g] = mk4<vec4, real>(aw, ae, (real)0, (real)0);
         }
