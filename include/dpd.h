@@ -226,6 +226,14 @@ int dpd_destroy(dpd_handle *h);
 #define DPD_WAIT_CHECK_MAX_TRIES (1 << 22)
 int dpd_wait_check(int32_t deliver, int32_t tries, void *cuda_stream);
 
+/* Check of the FP64 path's Box-Muller logarithm (a table-driven ln of the
+ * uniforms u = n 2^-24, n odd, after P. T. P. Tang, ACM TOMS 16, 1990) against
+ * the CUDA library's log over all 2^23 inputs: *max_abs_err receives the
+ * largest absolute difference.  Allocates and frees its own device memory on
+ * the current device; synchronises.  DPD_EINVAL if max_abs_err is NULL,
+ * DPD_ECUDA if a CUDA call fails. */
+int dpd_ln_check(double *max_abs_err);
+
 /* ---- batches: many independent systems advanced by the same launches ----
  * A batch owns fixed pools sized at creation.  Systems are added (with their
  * state) and removed at any time between steps; dpd_batch_step advances

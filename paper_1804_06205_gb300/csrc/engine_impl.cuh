@@ -125,6 +125,11 @@ class BatchEngine : public BatchBase {
             (rc = alloc(&obs_, (size_t)NS_ * RED_K)) || (rc = alloc(&acc_, (size_t)NS_ * 4)) ||
             (rc = alloc(&old_bead0_, (size_t)NS_)))
             return rc;
+        if (!P::kOffsets) {   // FP64 Box-Muller logarithm tables
+            if ((rc = alloc(&lntab_, 1))) return rc;
+            k_ln_tab<<<1, 128, 0, stream_>>>(lntab_);
+            DPD_CU(cudaGetLastError());
+        }
         for (auto &e : ph_) DPD_CU(cudaEventCreate(&e));
         for (auto &e : xev_) DPD_CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         DPD_CU(cudaStreamCreateWithFlags(&xfer_, cudaStreamNonBlocking));
@@ -772,6 +777,7 @@ class BatchEngine : public BatchBase {
         pl.capmax = capmax_;
         pl.Xmax = xmax_;
         pl.ntmax = ntmax_;
+        pl.lntab = lntab_;
         pl.pos = pos_;
         pl.vt = vt_;
         pl.key = key_;
@@ -1053,6 +1059,7 @@ class BatchEngine : public BatchBase {
          *frc_[2] = {nullptr, nullptr}, *vt_ = nullptr, *fpair_ = nullptr, *ev_ = nullptr;
     uint32_t *key_ = nullptr, *key_tmp_ = nullptr, *rank_ = nullptr, *src_ = nullptr;
     int32_t *sid_ = nullptr, *id_[2] = {nullptr, nullptr}, *inv_perm_ = nullptr, *types_ = nullptr;
+    LnTab *lntab_ = nullptr;
     int *bsys_ = nullptr, *brick_sys_ = nullptr, *old_bead0_ = nullptr;
     uint32_t *count_ = nullptr, *cell_start_ = nullptr, *bsum_ = nullptr;
     SysDesc<P> *sys_ = nullptr;

@@ -131,18 +131,53 @@ __device__ __forceinline__ double fma_rn(double a, double b, double c) { return 
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
 
-// theta from Box-Muller on outputs 0 and 1 (noise 0) or sqrt(3)(2u-1) (noise 1).
-__device__ __forceinline__ float theta_of(uint2 x, int noise, float) {
-    const float u0 = u01_f32(x.x);
-    if (noise) return 1.7320508075688772f * (2.0f * u0 - 1.0f);
-    const float u1 = u01_f32(x.y);
-    return sqrtf(-2.0f * logf(u0)) * cospif(2.0f * u1);
+// ln(u) for the uniforms u = n 2^-24 (n odd, n < 2^24) of the FP64 path, by the
+// table-driven method of P. T. P. Tang (ACM TOMS 16, 1990): with e = floor(log2 n)
+// and j the next seven bits of n, n = 2^e (1 + j/128) + rest, and
+//   ln u = (e - 24) ln 2 + ln(1 + j/128) + log1p(r),  r = rest 2^-e / (1 + j/128),
+// |r| < 2^-7, log1p(r) by its Taylor series to r^7 / 7 (the next term is below
+// 2e-18).  The reduction is integer arithmetic; the tables are filled with the
+// library's log.  Ten FP64 operations instead of a general log.
+struct LnTab {
+    double2 c[128];   // ln(1 + j/128), 1 / (1 + j/128)
+    double e[24];     // (e - 24) ln 2
+};
+static __global__ void k_ln_tab(LnTab *t) {
+    const int j = threadIdx.x;
+    if (j < 128) {
+        const double c = 1.0 + j / 128.0;
+        t->c[j] = make_double2(log(c), 1.0 / c);
+    }
+    if (j < 24) t->e[j] = (double)(j - 24) * log(2.0);
 }
-__device__ __forceinline__ double theta_of(uint2 x, int noise, double) {
-    const double u0 = u01_f64(x.x);
-    if (noise) return 1.7320508075688772 * (2.0 * u0 - 1.0);
+__device__ __forceinline__ double ln_u24(uint32_t n, const LnTab *t) {
+    const int e = 31 - __clz(n);
+    int j;
+    uint32_t rest;
+    if (e >= 7) {
+        j = (int)((n >> (e - 7)) & 127u);
+        rest = n & ((1u << (e - 7)) - 1u);
+    } else {
+        j = (int)((n << (7 - e)) & 127u);
+        rest = 0u;
+    }
+    const double2 cj = t->c[j];
+    // (1 + j/128)^-1 2^-e through the exponent field: exact, no underflow for e < 24
+    const double inv = __longlong_as_double(__double_as_longlong(cj.y) - ((long long)e << 52));
+    const double r = (double)rest * inv;
+    double p = fma(r, 1.0 / 7.0, -1.0 / 6.0);
+    p = fma(r, p, 1.0 / 5.0);
+    p = fma(r, p, -1.0 / 4.0);
+    p = fma(r, p, 1.0 / 3.0);
+    p = fma(r, p, -1.0 / 2.0);
+    p = fma(r, p, 1.0);
+    return t->e[e] + fma(r, p, cj.x);
+}
+// theta from Box-Muller on outputs 0 and 1 (noise 0) or sqrt(3)(2u-1) (noise 1).
+__device__ __forceinline__ double theta_of(uint2 x, int noise, const LnTab *lt) {
+    if (noise) return 1.7320508075688772 * (2.0 * u01_f64(x.x) - 1.0);
     const double u1 = u01_f64(x.y);
-    return sqrt(-2.0 * log(u0)) * cospi(2.0 * u1);
+    return sqrt(-2.0 * ln_u24((x.x >> 8) | 1u, lt)) * cospi(2.0 * u1);
 }
 
 // --------------------------------------------------------------------------
@@ -573,6 +608,7 @@ struct PairLaunch {   // a launch over bricks [br_lo, br_lo + gridDim.x) of any 
     const long long *counter;
     int *status;                        // sticky status bits (ST_TIMEOUT)
     int ntmax;                          // largest number of bead types (a_ij table size)
+    const LnTab *lntab;                 // FP64: tables of the Box-Muller logarithm
 };
 
 constexpr int PAIR_MAXX = 64;          // largest brick length (cells)
@@ -671,7 +707,7 @@ __device__ __forceinline__ uint2 philox_rk(uint32_t c0, uint32_t c1, uint32_t c2
 
 // Box-Muller with the fast intrinsics (FP32 path): -2 ln u0 = -2 ln2 log2 u0,
 // cos(2 pi u1) = -cos(2 pi u1 - pi) with the argument in (-pi, pi).
-__device__ __forceinline__ float theta_pair(uint2 x, int noise, float) {
+__device__ __forceinline__ float theta_pair(uint2 x, int noise, float, const LnTab *) {
     const float u0 = u01_f32(x.x);
     if (noise) return 1.7320508075688772f * (2.0f * u0 - 1.0f);
     const float u1 = u01_f32(x.y);
@@ -679,8 +715,8 @@ __device__ __forceinline__ float theta_pair(uint2 x, int noise, float) {
     const float s = q > 0.0f ? q * rsqrtf(q) : 0.0f;
     return -s * __cosf(fmaf(6.2831853071795865f, u1, -3.1415926535897932f));
 }
-__device__ __forceinline__ double theta_pair(uint2 x, int noise, double) {
-    return theta_of(x, noise, 0.0);
+__device__ __forceinline__ double theta_pair(uint2 x, int noise, double, const LnTab *lt) {
+    return theta_of(x, noise, lt);
 }
 
 template <class P, int T, bool SAMPLE>
@@ -989,7 +1025,7 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
                         const int32_t idi = P::unpack_int(iv.w), idj = P::unpack_int(vj.w);
                         const uint32_t lo = (uint32_t)min(idi, idj), hi = (uint32_t)max(idi, idj);
                         const uint2 rnd = philox_rk(lo, hi, s_lo, s_hi, rkl);
-                        const real th = theta_pair(rnd, a.noise, (real)0);
+                        const real th = theta_pair(rnd, a.noise, (real)0, la.lntab);
                         const real fc = mul_rn(aij, w);
                         const real gw2 = mul_rn(mul_rn(a.gamma, w), w);
                         const real mag = fma_rn(mul_rn(a.sig_sqdt, w), th, fma_rn(-gw2, evel, fc));

@@ -1,3 +1,5 @@
+// Self-checks of the device code that tests call through the C ABI.
+//
 // dpd_wait_check: failure detection of the bounded device waits, exercised
 // without a fault.  One block waits on an mbarrier with the same bounded poll
 // loop as the pair kernel's staging wait.  With deliver = 1 a bulk copy brings
@@ -6,7 +8,12 @@
 // `tries` polls and the block records ST_TIMEOUT and returns.  No copy is ever
 // left in flight, so the context stays usable.  The source and the status word
 // are file-scope device variables: the call allocates nothing.
+//
+// dpd_ln_check: the FP64 Box-Muller logarithm (ln_u24) against the library's
+// log over all 2^23 uniforms n 2^-24; returns the largest absolute difference.
 #include <cuda_runtime.h>
+
+#include <cstring>
 
 #include "dpd.h"
 #include "kernels.cuh"
@@ -37,7 +44,42 @@ __global__ void k_wait_check(int deliver, int tries) {
     if (threadIdx.x == 0 && buf[0] != g_wc_src[0]) atomicOr(&g_wc_status, dpd::ST_BADINPUT);
 }
 
+// |ln_u24(n) - log(n 2^-24)| over every odd n < 2^24, its maximum kept as the
+// bits of a non-negative double (which order like the doubles)
+__global__ void k_ln_check(const dpd::LnTab *t, unsigned long long *max_abs) {
+    double m = 0.0;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < (1u << 23);
+         k += gridDim.x * blockDim.x) {
+        const uint32_t n = 2u * k + 1u;
+        m = fmax(m, fabs(dpd::ln_u24(n, t) - log((double)n * 0x1p-24)));
+    }
+    atomicMax(max_abs, (unsigned long long)__double_as_longlong(m));
+}
+
 }  // namespace
+
+extern "C" int dpd_ln_check(double *max_abs_err) {
+    if (!max_abs_err) return DPD_EINVAL;
+    dpd::LnTab *t = nullptr;
+    unsigned long long *m = nullptr, mh = 0;
+    int rc = DPD_OK;
+    if (cudaMalloc(&t, sizeof(dpd::LnTab)) != cudaSuccess ||
+        cudaMalloc(&m, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(m, 0, sizeof(unsigned long long)) != cudaSuccess) {
+        rc = DPD_ECUDA;
+    } else {
+        dpd::k_ln_tab<<<1, 128>>>(t);
+        k_ln_check<<<1024, 256>>>(t, m);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpy(&mh, m, sizeof(mh), cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = DPD_ECUDA;
+        else
+            std::memcpy(max_abs_err, &mh, sizeof(double));
+    }
+    if (t) cudaFree(t);
+    if (m) cudaFree(m);
+    return rc;
+}
 
 extern "C" int dpd_wait_check(int32_t deliver, int32_t tries, void *cuda_stream) {
     if (tries <= 0 || tries > DPD_WAIT_CHECK_MAX_TRIES) return DPD_EINVAL;
