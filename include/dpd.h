@@ -226,13 +226,14 @@ int dpd_destroy(dpd_handle *h);
 #define DPD_WAIT_CHECK_MAX_TRIES (1 << 22)
 int dpd_wait_check(int32_t deliver, int32_t tries, void *cuda_stream);
 
-/* Check of the FP64 path's Box-Muller logarithm (a table-driven ln of the
- * uniforms u = n 2^-24, n odd, after P. T. P. Tang, ACM TOMS 16, 1990) against
- * the CUDA library's log over all 2^23 inputs: *max_abs_err receives the
- * largest absolute difference.  Allocates and frees its own device memory on
- * the current device; synchronises.  DPD_EINVAL if max_abs_err is NULL,
- * DPD_ECUDA if a CUDA call fails. */
-int dpd_ln_check(double *max_abs_err);
+/* Check of the FP64 path's Box-Muller functions of the uniforms u = n 2^-24
+ * (n odd): the table-driven ln u (after P. T. P. Tang, ACM TOMS 16, 1990) and
+ * cos(2 pi u) with exact quadrant reduction, against the CUDA library's log and
+ * cospi over all 2^23 inputs.  *ln_err and *cos_err receive the largest
+ * absolute differences.  Allocates and frees its own device memory on the
+ * current device; synchronises.  DPD_EINVAL if a pointer is NULL, DPD_ECUDA if
+ * a CUDA call fails. */
+int dpd_bm_check(double *ln_err, double *cos_err);
 
 /* ---- batches: many independent systems advanced by the same launches ----
  * A batch owns fixed pools sized at creation.  Systems are added (with their

@@ -173,11 +173,36 @@ __device__ __forceinline__ double ln_u24(uint32_t n, const LnTab *t) {
     p = fma(r, p, 1.0);
     return t->e[e] + fma(r, p, cj.x);
 }
+// cos(2 pi v) for the uniforms v = a 2^-24 (a odd, a < 2^24) of the FP64 path.
+// The quadrant is a's top two bits, so the reduction is exact integer
+// arithmetic: with b the remaining 22 bits, 2 pi v = q pi/2 + (pi/2) b 2^-22,
+// and cos(q pi/2 + phi) = +-cos(psi) with psi = phi (q even) or pi/2 - phi (q
+// odd), psi = (pi/2) c 2^-22 in [0, pi/2].  cos(psi) is its Taylor series to
+// psi^22 / 22! (the next term is below 1e-19).
+__device__ __forceinline__ double cos_u24(uint32_t a) {
+    const uint32_t q = a >> 22, b = a & 0x3FFFFFu;
+    const uint32_t c = (q & 1u) ? 0x400000u - b : b;
+    const double psi = (double)c * (3.141592653589793 / 8388608.0);   // c pi 2^-23, pi/2^23 exact
+    const double s = psi * psi;
+    double p = -1.0 / 1124000727777607680000.0;
+    p = fma(s, p, 1.0 / 2432902008176640000.0);
+    p = fma(s, p, -1.0 / 6402373705728000.0);
+    p = fma(s, p, 1.0 / 20922789888000.0);
+    p = fma(s, p, -1.0 / 87178291200.0);
+    p = fma(s, p, 1.0 / 479001600.0);
+    p = fma(s, p, -1.0 / 3628800.0);
+    p = fma(s, p, 1.0 / 40320.0);
+    p = fma(s, p, -1.0 / 720.0);
+    p = fma(s, p, 1.0 / 24.0);
+    p = fma(s, p, -1.0 / 2.0);
+    p = fma(s, p, 1.0);
+    return (q == 1u || q == 2u) ? -p : p;
+}
+
 // theta from Box-Muller on outputs 0 and 1 (noise 0) or sqrt(3)(2u-1) (noise 1).
 __device__ __forceinline__ double theta_of(uint2 x, int noise, const LnTab *lt) {
     if (noise) return 1.7320508075688772 * (2.0 * u01_f64(x.x) - 1.0);
-    const double u1 = u01_f64(x.y);
-    return sqrt(-2.0 * ln_u24((x.x >> 8) | 1u, lt)) * cospi(2.0 * u1);
+    return sqrt(-2.0 * ln_u24((x.x >> 8) | 1u, lt)) * cos_u24((x.y >> 8) | 1u);
 }
 
 // --------------------------------------------------------------------------

@@ -9,8 +9,9 @@
 // left in flight, so the context stays usable.  The source and the status word
 // are file-scope device variables: the call allocates nothing.
 //
-// dpd_ln_check: the FP64 Box-Muller logarithm (ln_u24) against the library's
-// log over all 2^23 uniforms n 2^-24; returns the largest absolute difference.
+// dpd_bm_check: the FP64 Box-Muller logarithm and cosine (ln_u24, cos_u24)
+// against the library's log and cospi over all 2^23 uniforms n 2^-24; returns
+// the largest absolute differences.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -44,37 +45,43 @@ __global__ void k_wait_check(int deliver, int tries) {
     if (threadIdx.x == 0 && buf[0] != g_wc_src[0]) atomicOr(&g_wc_status, dpd::ST_BADINPUT);
 }
 
-// |ln_u24(n) - log(n 2^-24)| over every odd n < 2^24, its maximum kept as the
-// bits of a non-negative double (which order like the doubles)
-__global__ void k_ln_check(const dpd::LnTab *t, unsigned long long *max_abs) {
-    double m = 0.0;
+// |ln_u24(n) - log(n 2^-24)| and |cos_u24(n) - cospi(2 n 2^-24)| over every odd
+// n < 2^24, their maxima kept as the bits of non-negative doubles (which order
+// like the doubles)
+__global__ void k_bm_check(const dpd::LnTab *t, unsigned long long *max_abs) {
+    double ml = 0.0, mc = 0.0;
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < (1u << 23);
          k += gridDim.x * blockDim.x) {
         const uint32_t n = 2u * k + 1u;
-        m = fmax(m, fabs(dpd::ln_u24(n, t) - log((double)n * 0x1p-24)));
+        const double u = (double)n * 0x1p-24;
+        ml = fmax(ml, fabs(dpd::ln_u24(n, t) - log(u)));
+        mc = fmax(mc, fabs(dpd::cos_u24(n) - cospi(2.0 * u)));
     }
-    atomicMax(max_abs, (unsigned long long)__double_as_longlong(m));
+    atomicMax(max_abs, (unsigned long long)__double_as_longlong(ml));
+    atomicMax(max_abs + 1, (unsigned long long)__double_as_longlong(mc));
 }
 
 }  // namespace
 
-extern "C" int dpd_ln_check(double *max_abs_err) {
-    if (!max_abs_err) return DPD_EINVAL;
+extern "C" int dpd_bm_check(double *ln_err, double *cos_err) {
+    if (!ln_err || !cos_err) return DPD_EINVAL;
     dpd::LnTab *t = nullptr;
-    unsigned long long *m = nullptr, mh = 0;
+    unsigned long long *m = nullptr, mh[2] = {0, 0};
     int rc = DPD_OK;
     if (cudaMalloc(&t, sizeof(dpd::LnTab)) != cudaSuccess ||
-        cudaMalloc(&m, sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMemset(m, 0, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMalloc(&m, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(m, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) {
         rc = DPD_ECUDA;
     } else {
         dpd::k_ln_tab<<<1, 128>>>(t);
-        k_ln_check<<<1024, 256>>>(t, m);
+        k_bm_check<<<1024, 256>>>(t, m);
         if (cudaGetLastError() != cudaSuccess ||
-            cudaMemcpy(&mh, m, sizeof(mh), cudaMemcpyDeviceToHost) != cudaSuccess)
+            cudaMemcpy(mh, m, sizeof(mh), cudaMemcpyDeviceToHost) != cudaSuccess) {
             rc = DPD_ECUDA;
-        else
-            std::memcpy(max_abs_err, &mh, sizeof(double));
+        } else {
+            std::memcpy(ln_err, &mh[0], sizeof(double));
+            std::memcpy(cos_err, &mh[1], sizeof(double));
+        }
     }
     if (t) cudaFree(t);
     if (m) cudaFree(m);

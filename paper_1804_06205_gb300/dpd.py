@@ -36,7 +36,7 @@ EXPORTED = ("dpd_default_options", "dpd_create", "dpd_set_state", "dpd_step", "d
             "dpd_batch_add", "dpd_batch_remove", "dpd_batch_step", "dpd_batch_get_state",
             "dpd_batch_observables", "dpd_batch_usage", "dpd_batch_sync", "dpd_batch_launch_count",
             "dpd_batch_last_error", "dpd_batch_destroy", "dpd_batch_profile_begin",
-            "dpd_batch_profile_end", "dpd_wait_check", "dpd_ln_check")
+            "dpd_batch_profile_end", "dpd_wait_check", "dpd_bm_check")
 
 
 class dpd_box(C.Structure):
@@ -108,8 +108,8 @@ def _load():
     lib.dpd_cells_noalloc.argtypes = [P, C.c_int64, P, P, P, P, P]
     lib.dpd_wait_check.argtypes = [C.c_int32, C.c_int32, P]
     lib.dpd_wait_check.restype = C.c_int
-    lib.dpd_ln_check.argtypes = [P]
-    lib.dpd_ln_check.restype = C.c_int
+    lib.dpd_bm_check.argtypes = [P, P]
+    lib.dpd_bm_check.restype = C.c_int
     lib.dpd_batch_create.argtypes = [P, P, P]
     lib.dpd_batch_add.argtypes = [P, P, C.c_int64, P, C.c_int32, P, C.c_double, C.c_double,
                                   C.c_double, P, C.c_int64, P, C.c_int64, C.c_double, C.c_uint64,
@@ -166,14 +166,15 @@ def wait_check(deliver, tries=4096, stream_ptr=None):
     return lib.dpd_wait_check(1 if deliver else 0, int(tries), C.c_void_p(stream_ptr))
 
 
-def ln_check():
-    """dpd_ln_check: largest absolute difference between the FP64 Box-Muller
-    logarithm and the library log over all 2^23 uniforms."""
-    err = C.c_double(0.0)
-    rc = lib.dpd_ln_check(C.byref(err))
+def bm_check():
+    """dpd_bm_check: largest absolute differences (ln, cos) between the FP64
+    Box-Muller functions and the library's log and cospi over all 2^23
+    uniforms."""
+    le, ce = C.c_double(0.0), C.c_double(0.0)
+    rc = lib.dpd_bm_check(C.byref(le), C.byref(ce))
     if rc != DPD_OK:
-        raise DPDError(rc, "dpd_ln_check")
-    return err.value
+        raise DPDError(rc, "dpd_bm_check")
+    return le.value, ce.value
 
 
 def default_options(**kw) -> dpd_options:

@@ -12,8 +12,11 @@ def D():
     return dpd
 
 
-def test_box_muller_log_matches_library_log(D):
+def test_box_muller_functions_match_library(D):
     # every uniform n 2^-24 (n odd); |ln u| <= 16.7, so a few units in the last
-    # place of the largest values is ~1e-14: far below what the FP64 force
-    # tolerance (1e-10 max|f|) could notice in theta = sqrt(-2 ln u) cos(2 pi v)
-    assert D.ln_check() < 1e-14
+    # place of the largest values is ~1e-14, and |cos| <= 1: both far below
+    # what the FP64 force tolerance (1e-10 max|f|) could notice in
+    # theta = sqrt(-2 ln u) cos(2 pi v)
+    ln_err, cos_err = D.bm_check()
+    assert ln_err < 1e-14
+    assert cos_err < 1e-15
