@@ -540,8 +540,16 @@ class BatchEngine : public BatchBase {
     }
 
     // staging for one system's host <-> device copies (9 doubles per bead)
+    // Host-transfer staging for n beads (pos, vel, force as doubles).  Every
+    // earlier use has been synchronised, so a smaller buffer is freed at once.
     int ensure_io(size_t n) {
         if (io_n_ >= n) return DPD_OK;
+        if (io_) {
+            allocs_.erase(std::find(allocs_.begin(), allocs_.end(), (void *)io_));
+            cudaFree(io_);
+            io_ = nullptr;
+            io_n_ = 0;
+        }
         double *q = nullptr;
         const int rc = alloc(&q, 9 * n);
         if (rc) return rc;
