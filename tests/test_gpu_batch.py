@@ -63,14 +63,17 @@ def test_batched_systems_equal_alone_runs(D, prec):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_sampling_does_not_change_the_trajectory(D, prec):
-    """dpd_step samples the observables on its last step; sampled and plain
-    steps must give identical forces, so splitting a run changes nothing."""
+    """Splitting a run into calls changes which steps fuse the next position
+    update (the last step of a call does not), and observables asked for
+    between calls run a sampled force pass on the state: none of it may change
+    the trajectory."""
     w = systems()[4]
     ref = alone(D, w, 12, prec)
     g = D.System.from_workload(w, precision=prec)
     g.set_state(w.pos, w.vel, 0)
     for k in (5, 4, 1, 2):
         g.step(k)
+        assert np.isfinite(g.observables()["p_total"])
     got = g.get_state()
     for x, y in zip(got[:3], ref[:3]):
         assert np.array_equal(x, y)
@@ -93,6 +96,14 @@ def test_removal_repacks_and_keeps_the_others_exact(D):
         got = b.get_state(s)
         for x, y in zip(got[:3], ref[:3]):
             assert np.array_equal(x, y), w.name
+        # observables computed on demand from the re-packed pools
+        g = D.System.from_workload(w, precision=0)
+        g.set_state(w.pos, w.vel, 0)
+        g.step(12)
+        oa, ob = g.observables(), b.observables(s)
+        g.close()
+        for k in ("kT", "p_total", "e_pair", "e_bond"):
+            assert oa[k] == ob[k], (w.name, k)
     b.close()
 
 
