@@ -1,6 +1,6 @@
 // Device code of the DPD step loop (arxiv 1804.06205, Fig. 1) for sm_103a.
-// Included by engine_f32.cu and engine_f64.cu (one precision each) and by
-// cells_noalloc.cu (cell keys and scans only).
+// Included by engine_f32.cu and engine_f64.cu (one precision each), by
+// cells_noalloc.cu (cell keys and scans only) and by selfcheck.cu.
 //
 // Every kernel works on any number of resident systems at once: the systems
 // are packed one after another in shared bead, cell, brick and bond pools, a
@@ -10,16 +10,21 @@
 // sort orders all systems at once.  Ids, cell keys and Philox counters are
 // local to a system, so a system computes the same numbers alone or packed.
 //
-// One step (Fig. 1), all on the device:
+// One step (Fig. 1), all on the device; each kernel starts with
+// griddep_wait, so the host may launch them back to back with programmatic
+// dependent launch:
 //   k_update      1.-2. r += dt v + dt^2/2 f, periodic wrap, new cell key,
-//                 cell occupancy histogram (atomics on counts)
+//                 cell occupancy histogram (atomics on counts); usually done
+//                 instead by the previous step's k_bond_vel (update_bead)
 //   k_scan*       3.    exclusive scan of the counts -> cell_start
 //   k_scatter     3.    slot = cell_start[key] + arrival rank
 //   k_gather      3.    canonical (cell, id) order: each arrival ranks itself among
 //                       its cell's ids and moves its state there; v~ = v + lambda dt f
 //   k_pair        4.    eq. 3-4 + dissipative/random pair terms, 27-cell full shell
 //   k_bond_vel    4.-5. eqs. 6-8 bonded terms, then v += dt/2 (f + f')
-//   k_reduce*           FP64 sums for the observables (sampled steps only)
+//   k_reduce*           FP64 sums for the observables (steps that sample running
+//                       means; observables asked for between steps, after a
+//                       sampled k_pair and k_bond_obs)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -580,7 +585,7 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs<P> a) {
 
 // --------------------------------------------------------------------------
 // a4-a5: pair forces, 27-cell full shell: every bead's force is summed in a
-// fixed order by its own warp, with no force atomics.
+// fixed order by one thread, with no force atomics.
 //
 // A block owns a brick of X x BY x BZ home cells (BY, BZ <= 2).  It stages the
 // (BY+2)(BZ+2) neighbouring x-row runs (X+2 cells each, periodic) into shared
@@ -592,9 +597,15 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs<P> a) {
 //
 // Each warp takes 32 home beads (one per lane) and alternates two phases:
 //   scan     every lane records its hits r^2 < 1 in row and slot order in its
-//            own queue, at most PAIR_HMAX per pass;
+//            own queue, at most PAIR_HMAX per pass (binary32 on both paths;
+//            FP64 queues every pair with binary32 r^2 < 1.001 and the
+//            evaluation applies the exact FP64 test);
 //   evaluate every lane evaluates its own queue in order and adds the pair
-//            forces to its bead's sums in registers.
+//            forces to its bead's sums in registers.  FP64, when a block
+//            needs one chunk and one pass: thread t evaluates the queue of
+//            the block's bead of rank t by hit count, so that a warp's
+//            queues have similar lengths (idle lanes still hold the FP64
+//            pipe).
 // Passes repeat until all 27 cells are done; oversized neighbourhoods are
 // staged in chunks.  Each bead's force is summed in a fixed order, so runs
 // are deterministic; another brick shape changes only the order of the
