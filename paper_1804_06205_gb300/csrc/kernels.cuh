@@ -1044,33 +1044,74 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
         auto evaluate = [&](const uint16_t *qb, int col, int n, const vec4 &ip, const vec4 &iv,
                             real &sx, real &sy, real &sz, real &sw, real &se) {
                 const int nmax = (int)__reduce_max_sync(FULL, (unsigned)n);
-                for (int m = 0; m < nmax; ++m) {
-                    if (m < n) {
-                        const int jl = qb[m * 32 + col];
-                        const vec4 pj = s_pos[jl], vj = s_vt[jl];
-                        const real dx = ip.x - pj.x, dyv = ip.y - pj.y, dzv = ip.z - pj.z;
-                        const real r2 = fma_rn(dzv, dzv, fma_rn(dyv, dyv, mul_rn(dx, dx)));
-                        if (!P::kOffsets && !(r2 < (real)1 && r2 > (real)0)) continue;
-                        const real rinv = rsqrt_r(r2);
-                        const real rr1 = mul_rn(r2, rinv);
-                        const real w = (real)1 - rr1;
-                        const real ex = mul_rn(dx, rinv), ey = mul_rn(dyv, rinv), ez = mul_rn(dzv, rinv);
-                        const real evel = fma_rn(ez, iv.z - vj.z,
-                                                 fma_rn(ey, iv.y - vj.y, mul_rn(ex, iv.x - vj.x)));
-                        const real aij = s_a[P::unpack_int(ip.w) * nt + P::unpack_int(pj.w)];
-                        const int32_t idi = P::unpack_int(iv.w), idj = P::unpack_int(vj.w);
-                        const uint32_t lo = (uint32_t)min(idi, idj), hi = (uint32_t)max(idi, idj);
-                        const uint2 rnd = philox_rk(lo, hi, s_lo, s_hi, rkl);
-                        const real th = theta_pair(rnd, a.noise, (real)0, la.lntab);
-                        const real fc = mul_rn(aij, w);
-                        const real gw2 = mul_rn(mul_rn(a.gamma, w), w);
-                        const real mag = fma_rn(mul_rn(a.sig_sqdt, w), th, fma_rn(-gw2, evel, fc));
-                        sx = add_rn(sx, mul_rn(mag, ex));
-                        sy = add_rn(sy, mul_rn(mag, ey));
-                        sz = add_rn(sz, mul_rn(mag, ez));
-                        if (SAMPLE) {
-                            sw += rr1 * fc;
-                            se += (real)0.5 * fc * w;
+                if constexpr (P::kOffsets) {
+                    // binary32: pj - pi and vj - vi (negated differences, the same r^2
+                    // and e.v) with x and y packed; each term is added to the sums with
+                    // one explicit fused multiply-add (x and y packed, kept negated),
+                    // so every kernel variant rounds the sums the same way
+                    const float2 nip = make_float2(-ip.x, -ip.y), niv = make_float2(-iv.x, -iv.y);
+                    float2 ns = make_float2(0.0f - sx, 0.0f - sy);
+                    for (int m = 0; m < nmax; ++m) {
+                        if (m < n) {
+                            const int jl = qb[m * 32 + col];
+                            const vec4 pj = s_pos[jl], vj = s_vt[jl];
+                            const float2 d = __fadd2_rn(make_float2(pj.x, pj.y), nip);
+                            const float dzv = pj.z - ip.z;
+                            const float r2 = fma_rn(dzv, dzv, fma_rn(d.y, d.y, mul_rn(d.x, d.x)));
+                            const float rinv = rsqrt_r(r2);
+                            const float rr1 = mul_rn(r2, rinv);
+                            const float w = 1.0f - rr1;
+                            const float2 e = __fmul2_rn(d, make_float2(rinv, rinv));
+                            const float ez = mul_rn(dzv, rinv);
+                            const float2 dv = __fadd2_rn(make_float2(vj.x, vj.y), niv);
+                            const float evel = fma_rn(ez, vj.z - iv.z, fma_rn(e.y, dv.y, mul_rn(e.x, dv.x)));
+                            const float aij = s_a[P::unpack_int(ip.w) * nt + P::unpack_int(pj.w)];
+                            const int32_t idi = P::unpack_int(iv.w), idj = P::unpack_int(vj.w);
+                            const uint32_t lo = (uint32_t)min(idi, idj), hi = (uint32_t)max(idi, idj);
+                            const uint2 rnd = philox_rk(lo, hi, s_lo, s_hi, rkl);
+                            const float th = theta_pair(rnd, a.noise, 0.0f, la.lntab);
+                            const float fc = mul_rn(aij, w);
+                            const float gw2 = mul_rn(mul_rn(a.gamma, w), w);
+                            const float mag = fma_rn(mul_rn(a.sig_sqdt, w), th, fma_rn(-gw2, evel, fc));
+                            ns = __ffma2_rn(make_float2(mag, mag), e, ns);
+                            sz = __fmaf_rn(-mag, ez, sz);
+                            if (SAMPLE) {
+                                sw += rr1 * fc;
+                                se += 0.5f * fc * w;
+                            }
+                        }
+                    }
+                    sx = 0.0f - ns.x;
+                    sy = 0.0f - ns.y;
+                } else {   // FP64
+                    for (int m = 0; m < nmax; ++m) {
+                        if (m < n) {
+                            const int jl = qb[m * 32 + col];
+                            const vec4 pj = s_pos[jl], vj = s_vt[jl];
+                            const real dx = ip.x - pj.x, dyv = ip.y - pj.y, dzv = ip.z - pj.z;
+                            const real r2 = fma_rn(dzv, dzv, fma_rn(dyv, dyv, mul_rn(dx, dx)));
+                            if (!P::kOffsets && !(r2 < (real)1 && r2 > (real)0)) continue;
+                            const real rinv = rsqrt_r(r2);
+                            const real rr1 = mul_rn(r2, rinv);
+                            const real w = (real)1 - rr1;
+                            const real ex = mul_rn(dx, rinv), ey = mul_rn(dyv, rinv), ez = mul_rn(dzv, rinv);
+                            const real evel = fma_rn(ez, iv.z - vj.z,
+                                                     fma_rn(ey, iv.y - vj.y, mul_rn(ex, iv.x - vj.x)));
+                            const real aij = s_a[P::unpack_int(ip.w) * nt + P::unpack_int(pj.w)];
+                            const int32_t idi = P::unpack_int(iv.w), idj = P::unpack_int(vj.w);
+                            const uint32_t lo = (uint32_t)min(idi, idj), hi = (uint32_t)max(idi, idj);
+                            const uint2 rnd = philox_rk(lo, hi, s_lo, s_hi, rkl);
+                            const real th = theta_pair(rnd, a.noise, (real)0, la.lntab);
+                            const real fc = mul_rn(aij, w);
+                            const real gw2 = mul_rn(mul_rn(a.gamma, w), w);
+                            const real mag = fma_rn(mul_rn(a.sig_sqdt, w), th, fma_rn(-gw2, evel, fc));
+                            sx = add_rn(sx, mul_rn(mag, ex));
+                            sy = add_rn(sy, mul_rn(mag, ey));
+                            sz = add_rn(sz, mul_rn(mag, ez));
+                            if (SAMPLE) {
+                                sw += rr1 * fc;
+                                se += (real)0.5 * fc * w;
+                            }
                         }
                     }
                 }
@@ -1084,7 +1125,10 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
                 staged_lo = c0;
             }
             __syncwarp();
-            const float xs = (float)hp.x, ys = (float)hp.y, zs = (float)hp.z;
+            // minus the bead's coordinates: the scan forms pj - pi (the negated
+            // difference, same r^2), x and y in one packed binary32 add
+            const float2 nxy = make_float2(-(float)hp.x, -(float)hp.y);
+            const float nzs = -(float)hp.z;
             const uint16_t self =
                 (self_abs >= c0 && self_abs < c1) ? (uint16_t)(self_abs - c0) : (uint16_t)0xFFFF;
             int r9 = 0, q = 0;
@@ -1115,10 +1159,11 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
                             uint16_t *qp = my_q + nh * 32 + lane;
                             for (; q + 1 < qe; q += 2, pp += 2, ent += 2) {   // two at a time
                                 const float4 pa = pp[0], pb = pp[1];
-                                const float ax = xs - pa.x, ay = ys - pa.y, az = zs - pa.z;
-                                const float bx = xs - pb.x, by = ys - pb.y, bz = zs - pb.z;
-                                const float ra = fma_rn(az, az, fma_rn(ay, ay, mul_rn(ax, ax)));
-                                const float rb = fma_rn(bz, bz, fma_rn(by, by, mul_rn(bx, bx)));
+                                const float2 da = __fadd2_rn(make_float2(pa.x, pa.y), nxy);
+                                const float2 db = __fadd2_rn(make_float2(pb.x, pb.y), nxy);
+                                const float az = add_rn(pa.z, nzs), bz = add_rn(pb.z, nzs);
+                                const float ra = fma_rn(az, az, fma_rn(da.y, da.y, mul_rn(da.x, da.x)));
+                                const float rb = fma_rn(bz, bz, fma_rn(db.y, db.y, mul_rn(db.x, db.x)));
                                 if (ra < scan_lim && (P::kOffsets ? ra > 0.0f : ent != self)) {
                                     *qp = ent;
                                     qp += 32;
@@ -1131,8 +1176,9 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
                             }
                             if (q < qe) {
                                 const float4 pj = *pp;
-                                const float dx = xs - pj.x, dyv = ys - pj.y, dzv = zs - pj.z;
-                                const float r2 = fma_rn(dzv, dzv, fma_rn(dyv, dyv, mul_rn(dx, dx)));
+                                const float2 d = __fadd2_rn(make_float2(pj.x, pj.y), nxy);
+                                const float dzv = add_rn(pj.z, nzs);
+                                const float r2 = fma_rn(dzv, dzv, fma_rn(d.y, d.y, mul_rn(d.x, d.x)));
                                 if (r2 < scan_lim && (P::kOffsets ? r2 > 0.0f : ent != self)) {
                                     *qp = ent;
                                     qp += 32;
