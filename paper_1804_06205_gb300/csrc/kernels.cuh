@@ -829,36 +829,42 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
     const real hx = a.h[0], hy = a.h[1], hz = a.h[2];
 
     for (int e = tid; e < a.ntypes * a.ntypes; e += T) s_a[e] = a.a[e];
-    // per staged cell: counts (k = 0..Xe+1 <-> ux = -1..Xe), k = Xe+2 is the row end
-    for (int r = wid; r < NRe; r += NW) {
+    // per staged cell: counts (k = 0..Xe+1 <-> ux = -1..Xe), k = Xe+2 is the row end;
+    // the threads share the flattened (row, cell) grid, so that many cell-start
+    // loads are in flight at once
+#pragma unroll 2
+    for (int e = tid; e < NRe * W; e += T) {
+        const int r = e / W, k = e - r * W;
+        int cnt = 0, first = 0;
+        if (k <= Xe + 1) {
+            const int uy = r % SY - 1, uz = r / SY - 1;
+            int yy = y0 + uy, zz = z0 + uz, xx = x0 + k - 1;
+            yy += yy < 0 ? a.ny : (yy >= a.ny ? -a.ny : 0);
+            zz += zz < 0 ? a.nz : (zz >= a.nz ? -a.nz : 0);
+            xx += xx < 0 ? a.nx : (xx >= a.nx ? -a.nx : 0);
+            const uint32_t c = ((uint32_t)zz * a.ny + yy) * a.nx + xx;
+            first = (int)a.cell_start[c];
+            cnt = (int)a.cell_start[c + 1] - first;
+        }
+        s_cs[e] = cnt;
+        s_src[e] = first;
+    }
+    if (tid < NRe) {   // each staged row's frame shift
+        const int r = tid;
         const int uy = r % SY - 1, uz = r / SY - 1;
         int yy = y0 + uy, zz = z0 + uz;
         yy += yy < 0 ? a.ny : (yy >= a.ny ? -a.ny : 0);
         zz += zz < 0 ? a.nz : (zz >= a.nz ? -a.nz : 0);
-        const uint32_t rowkey = ((uint32_t)zz * a.ny + yy) * a.nx;
-        for (int k = lane; k < W; k += 32) {
-            int cnt = 0, first = 0;
-            if (k <= Xe + 1) {
-                int xx = x0 + k - 1;
-                xx += xx < 0 ? a.nx : (xx >= a.nx ? -a.nx : 0);
-                first = (int)a.cell_start[rowkey + xx];
-                cnt = (int)a.cell_start[rowkey + xx + 1] - first;
-            }
-            s_cs[r * W + k] = cnt;
-            s_src[r * W + k] = first;
+        real sy, sz;
+        if (P::kOffsets) {       // offset -> brick frame
+            sy = mul_rn((real)uy, hy);
+            sz = mul_rn((real)uz, hz);
+        } else {                 // absolute -> brick frame, undoing the row's wrap
+            sy = mul_rn((real)(uy - yy), hy);
+            sz = mul_rn((real)(uz - zz), hz);
         }
-        if (lane == 0) {
-            real sy, sz;
-            if (P::kOffsets) {       // offset -> brick frame
-                sy = mul_rn((real)uy, hy);
-                sz = mul_rn((real)uz, hz);
-            } else {                 // absolute -> brick frame, undoing the row's wrap
-                sy = mul_rn((real)(uy - yy), hy);
-                sz = mul_rn((real)(uz - zz), hz);
-            }
-            s_rsh[2 * r] = sy;
-            s_rsh[2 * r + 1] = sz;
-        }
+        s_rsh[2 * r] = sy;
+        s_rsh[2 * r + 1] = sz;
     }
     __syncthreads();
     if (tid < 32) {   // exclusive scan of the counts: staged start of each cell
