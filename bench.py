@@ -64,13 +64,13 @@ PAIR_OPS_PER_BEAD = 40.5 * 7 + 6.28 * 103
 SORT_BYTES_PER_BEAD = 172.0
 # DRAM bytes (read + written) per bead of one k_pair launch, from an ncu
 # capture of the current pair kernel on this workload (dram__bytes_read.sum +
-# dram__bytes_write.sum = 144.2 MB for 3,000,000 beads; the algorithmic
+# dram__bytes_write.sum = 144.8 MB for 3,000,000 beads; the algorithmic
 # minimum is 48 B per bead).
-PAIR_DRAM_BYTES_PER_BEAD = 48.08
+PAIR_DRAM_BYTES_PER_BEAD = 48.27
 # Thread instructions executed per bead by one k_pair launch, from the same
 # capture (smsp__inst_executed.sum x thread_inst_executed_per_inst_executed):
 # the issued work, against which the issue-rate roofline is taken.
-PAIR_THREAD_INST_PER_BEAD = 4480.0
+PAIR_THREAD_INST_PER_BEAD = 4384.0
 BOND_BYTES_PER_BEAD = 144.0
 
 
