@@ -183,6 +183,28 @@ int64_t dpd_launch_count(const dpd_handle *h);
 int dpd_profile_begin(dpd_handle *h, int64_t max_steps);
 int dpd_profile_end(dpd_handle *h, double ms[3], int64_t *nsteps);
 
+/* Checkpoint and resume (Fig. 1 carries r, v and the force f(t) from one
+ * step to the next, so a faithful restart needs all three).  A checkpoint is
+ * an opaque byte string: an 80-byte header (magic "DPDCKPT1", version,
+ * precision, n, the evaluation counter, cells per edge, record size, box and
+ * seed) followed by one record per bead in bead-id order holding the state in
+ * the engine's own representation -- FP32: cell key, cell-relative binary32
+ * offset, v and f (40 B); FP64: position, v and f (72 B) -- so that a system
+ * restored from it continues bit for bit as if it had never stopped.
+ * dpd_checkpoint_bytes: the size of the handle's checkpoint (host only).
+ * dpd_get_checkpoint: writes it to buf[bytes] (caller-allocated host memory,
+ *   bytes >= the size).  Synchronises.  Errors: DPD_EINVAL (NULL or short
+ *   buffer), DPD_ENOSTATE, DPD_ECUDA.
+ * dpd_set_checkpoint: replaces the state by the checkpoint's, with no force
+ *   evaluation; the handle must have been created with the same parameters
+ *   (precision, n, box and seed are checked against the header; types, a_ij,
+ *   bonds and the integrator parameters are the caller's responsibility).
+ *   Synchronises.  Errors: DPD_EINVAL (mismatched header, a cell key out of
+ *   range, a non-finite value; the previous state is then lost), DPD_ECUDA. */
+int dpd_checkpoint_bytes(const dpd_handle *h, int64_t *bytes);
+int dpd_get_checkpoint(dpd_handle *h, void *buf, int64_t bytes);
+int dpd_set_checkpoint(dpd_handle *h, const void *buf, int64_t bytes);
+
 /* Cell division without any allocation.  The paper has no counterpart: it
  * exists for callers that cannot call cudaMalloc -- code whose device memory
  * belongs to a framework allocator or a fixed, pre-budgeted arena, and code
@@ -202,6 +224,11 @@ int dpd_profile_end(dpd_handle *h, double ms[3], int64_t *nsteps);
  * all calls and keeping the last call's contents: calls that overlap on the
  * GPU race.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress), so make it before any stream capture.
+ * Cost: the canonical order inside a cell is found by every bead counting the
+ * cell's smaller ids, in parallel, so a cell holding k beads costs k loads per
+ * bead.  Physical states hold a few beads per cell; a degenerate input that
+ * puts all DPD_NOALLOC_MAX_N beads in one cell (for instance non-finite
+ * positions, which the key maps to cell 0) makes the call take seconds.
  * Errors: DPD_EINVAL for NULL pointers, a box edge < 3, n outside
  * [1, DPD_NOALLOC_MAX_N] or more than DPD_NOALLOC_MAX_CELLS cells;
  * DPD_ECUDA if the address lookup or a launch fails. */
@@ -286,6 +313,13 @@ int dpd_batch_observables(dpd_batch *b, int32_t sys, dpd_obs *out);
 /* Pool use: used[4] and cap[4] = beads, cells, bricks, bond records;
  * *nsys = resident systems.  Any pointer may be NULL. */
 int dpd_batch_usage(const dpd_batch *b, int64_t used[4], int64_t cap[4], int32_t *nsys);
+
+/* Checkpoints of one resident system, as dpd_checkpoint_bytes /
+ * dpd_get_checkpoint / dpd_set_checkpoint.  A checkpoint taken alone restores
+ * into a batch and the other way round (same parameters). */
+int dpd_batch_checkpoint_bytes(const dpd_batch *b, int32_t sys, int64_t *bytes);
+int dpd_batch_get_checkpoint(dpd_batch *b, int32_t sys, void *buf, int64_t bytes);
+int dpd_batch_set_checkpoint(dpd_batch *b, int32_t sys, const void *buf, int64_t bytes);
 
 int dpd_batch_sync(dpd_batch *b);
 int64_t dpd_batch_launch_count(const dpd_batch *b);

@@ -16,6 +16,11 @@
 // cudaGetSymbolAddress (with that device current) and caches it.  All calls
 // share the array and it keeps the last call's contents; calls that overlap
 // on the GPU (two streams, or two host threads) race on it.
+//
+// Steps: wrap + key + arrival rank (atomics on the counts), exclusive scan of
+// the counts, arrival-order scatter, then every bead finds its canonical slot
+// by counting the smaller ids of its cell (k loads for a cell of k beads, done
+// by all of them in parallel) and places itself there.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -89,6 +94,7 @@ __global__ void __launch_bounds__(dpd::SCAN_T) k_na_scan3(uint32_t *cs, int ncel
         }
 }
 
+// arrival order: order[cell start + arrival rank] = id
 __global__ void __launch_bounds__(256) k_na_scatter(int n, const uint32_t *key,
                                                     const uint32_t *rank, const uint32_t *cs,
                                                     int32_t *order) {
@@ -97,21 +103,25 @@ __global__ void __launch_bounds__(256) k_na_scatter(int n, const uint32_t *key,
     order[cs[key[i]] + rank[i]] = i;
 }
 
-// ids ascending inside each cell (insertion sort; cells hold a few beads)
-__global__ void __launch_bounds__(256) k_na_cellfix(int ncell, const uint32_t *cs,
-                                                    int32_t *order) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    const int b = (int)cs[c], e = (int)cs[c + 1];
-    for (int i = b + 1; i < e; ++i) {
-        const int32_t v = order[i];
-        int j = i - 1;
-        while (j >= b && order[j] > v) {
-            order[j + 1] = order[j];
-            --j;
-        }
-        order[j + 1] = v;
-    }
+// Canonical slot of every bead: its cell's start plus the number of the
+// cell's ids below its own (the cell's ids in arrival order are in `order`).
+// Every bead counts in parallel, so a cell of k beads costs k loads per bead;
+// slot[] reuses the arrival-rank words, which nothing reads any more.
+__global__ void __launch_bounds__(256) k_na_rank(int n, const uint32_t *key, const uint32_t *cs,
+                                                 const int32_t *order, uint32_t *slot) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t k = key[i];
+    const int b = (int)cs[k], e = (int)cs[k + 1];
+    int u = b;
+    for (int q = b; q < e; ++q) u += order[q] < i;
+    slot[i] = (uint32_t)u;
+}
+
+__global__ void __launch_bounds__(256) k_na_place(int n, const uint32_t *slot, int32_t *order) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    order[slot[i]] = i;
 }
 
 }  // namespace
@@ -133,9 +143,11 @@ extern "C" int dpd_cells_noalloc(const double *pos_dev, int64_t n, const dpd_box
         g.L[k] = L;
         g.h[k] = L / f;
         g.inv_h[k] = f / L;
+        // checked after every factor, so the product stays below 2^44 and the
+        // scan's block sums (sized for DPD_NOALLOC_MAX_CELLS) always suffice
         ncell *= (int64_t)nc[k];
+        if (ncell > DPD_NOALLOC_MAX_CELLS) return DPD_EINVAL;
     }
-    if (ncell > DPD_NOALLOC_MAX_CELLS) return DPD_EINVAL;   // the scan's block sums are sized for it
     g.nx = nc[0];
     g.ny = nc[1];
     g.nz = nc[2];
@@ -156,6 +168,7 @@ extern "C" int dpd_cells_noalloc(const double *pos_dev, int64_t n, const dpd_box
     dpd::k_scan2<<<1, dpd::SCAN_T, 0, st>>>(bsum, nb, cell_start_dev, C);
     k_na_scan3<<<nb, dpd::SCAN_T, 0, st>>>(cell_start_dev, C, bsum);
     k_na_scatter<<<(N + 255) / 256, 256, 0, st>>>(N, key_dev, rank, cell_start_dev, order_dev);
-    k_na_cellfix<<<(C + 255) / 256, 256, 0, st>>>(C, cell_start_dev, order_dev);
+    k_na_rank<<<(N + 255) / 256, 256, 0, st>>>(N, key_dev, cell_start_dev, order_dev, rank);
+    k_na_place<<<(N + 255) / 256, 256, 0, st>>>(N, rank, order_dev);
     return cudaGetLastError() == cudaSuccess ? DPD_OK : DPD_ECUDA;
 }

@@ -82,18 +82,23 @@ int build_config(const dpd_box *box, int64_t n, const int32_t *types, int32_t nt
         return bad("gamma, kT must be >= 0 and dt > 0");
     if (!is_fin(lambda)) return bad("lambda not finite");
     if (noise != DPD_NOISE_GAUSS && noise != DPD_NOISE_UNIFORM) return bad("bad noise");
+    // cells per edge and their product are checked before any conversion or
+    // multiplication could overflow: each factor is at most 2^31 - 2 and the
+    // running product never exceeds it either
+    const int64_t kMaxCells = ((int64_t)1 << 31) - 2;
     int64_t ncell = 1;
     for (int k = 0; k < 3; ++k) {
         const double L = box->L[k];
         if (!is_fin(L) || L < 3.0) return bad("every box edge must be >= 3");
         const double nc = std::floor(L);
+        if (nc > (double)kMaxCells) return bad("too many cells");
+        ncell *= (int64_t)nc;
+        if (ncell > kMaxCells) return bad("too many cells");
         c.L[k] = L;
         c.nc[k] = (int32_t)nc;
         c.h[k] = L / nc;
         c.inv_h[k] = nc / L;
-        ncell *= (int64_t)nc;
     }
-    if (ncell > ((int64_t)1 << 31) - 2) return bad("too many cells");
     c.n = n;
     c.ntypes = ntypes;
     c.types.assign(types, types + n);
@@ -236,6 +241,23 @@ int dpd_gr(dpd_handle *h, double rmax, int32_t nbins, uint64_t *counts) {
 int dpd_get_cells(dpd_handle *h, uint32_t *key_by_id, int64_t *order, int64_t *cell_start) {
     if (!h) return DPD_EINVAL;
     return h->eng->get_cells(h->slot, key_by_id, order, cell_start);
+}
+
+int dpd_checkpoint_bytes(const dpd_handle *h, int64_t *bytes) {
+    if (!h || !bytes) return DPD_EINVAL;
+    *bytes = h->eng->checkpoint_bytes(h->slot);
+    return DPD_OK;
+}
+
+int dpd_get_checkpoint(dpd_handle *h, void *buf, int64_t bytes) {
+    if (!h) return DPD_EINVAL;
+    return h->eng->get_checkpoint(h->slot, buf, bytes);
+}
+
+int dpd_set_checkpoint(dpd_handle *h, const void *buf, int64_t bytes) {
+    if (!h) return DPD_EINVAL;
+    h->err.clear();
+    return h->eng->set_checkpoint(h->slot, buf, bytes);
 }
 
 int dpd_cell_dims(const dpd_handle *h, int64_t nc[3]) {
@@ -386,6 +408,23 @@ int dpd_batch_usage(const dpd_batch *b, int64_t used[4], int64_t cap[4], int32_t
     }
     if (nsys) *nsys = b->eng->nlive();
     return DPD_OK;
+}
+
+int dpd_batch_checkpoint_bytes(const dpd_batch *b, int32_t sys, int64_t *bytes) {
+    if (!b || !bytes) return DPD_EINVAL;
+    *bytes = b->eng->checkpoint_bytes(sys);
+    return *bytes > 0 ? DPD_OK : DPD_EINVAL;
+}
+
+int dpd_batch_get_checkpoint(dpd_batch *b, int32_t sys, void *buf, int64_t bytes) {
+    if (!b) return DPD_EINVAL;
+    return b->eng->get_checkpoint(sys, buf, bytes);
+}
+
+int dpd_batch_set_checkpoint(dpd_batch *b, int32_t sys, const void *buf, int64_t bytes) {
+    if (!b) return DPD_EINVAL;
+    b->err.clear();
+    return b->eng->set_checkpoint(sys, buf, bytes);
 }
 
 int dpd_batch_sync(dpd_batch *b) {

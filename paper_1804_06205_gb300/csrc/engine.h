@@ -32,6 +32,19 @@ struct Config {
     double h[3], inv_h[3];
 };
 
+// Leading bytes of a checkpoint; the records follow in bead-id order.
+struct CkptHeader {
+    char magic[8];          // "DPDCKPT1"
+    uint32_t version;       // 1
+    int32_t precision;      // DPD_FP32 / DPD_FP64
+    int64_t n, step;        // beads, evaluation counter of the stored force
+    int32_t nc[3];          // cells per edge
+    uint32_t record_bytes;  // 40 (FP32) or 72 (FP64)
+    double L[3];            // box
+    uint64_t seed;          // Philox key
+};
+static_assert(sizeof(CkptHeader) == 80, "checkpoint header layout");
+
 // The pools of a batch and the engine-wide options.
 struct BatchConfig {
     int64_t max_beads, max_cells, max_bonds;   // bond records count both ends
@@ -55,6 +68,10 @@ class BatchBase {
     virtual int observables(int slot, dpd_obs *out) = 0;
     virtual int gr(int slot, double rmax, int32_t nbins, uint64_t *counts) = 0;
     virtual int get_cells(int slot, uint32_t *key_by_id, int64_t *order, int64_t *cell_start) = 0;
+    // Checkpoint of one system: header + per-bead records (CkptHeader below).
+    virtual int64_t checkpoint_bytes(int slot) const = 0;
+    virtual int get_checkpoint(int slot, void *buf, int64_t bytes) = 0;
+    virtual int set_checkpoint(int slot, const void *buf, int64_t bytes) = 0;
     virtual int sync() = 0;
     virtual int64_t launches() const = 0;
     virtual int profile_begin(int64_t max_steps) = 0;

@@ -479,6 +479,112 @@ class BatchEngine : public BatchBase {
         return check_status();
     }
 
+    // ------------------------------------------------------------ checkpoints
+    using Rec = typename CkptRec<P>::type;
+
+    int64_t checkpoint_bytes(int s) const override {
+        if (s < 0 || s >= NS_ || !hs_[s].live) return 0;
+        return (int64_t)sizeof(CkptHeader) + (int64_t)hs_[s].n * (int64_t)sizeof(Rec);
+    }
+
+    int get_checkpoint(int s, void *buf, int64_t bytes) override {
+        if (s < 0 || s >= NS_ || !hs_[s].live || !buf) return DPD_EINVAL;
+        SysHost &h = hs_[s];
+        if (!h.has_state) return DPD_ENOSTATE;
+        if (bytes < checkpoint_bytes(s)) {
+            err_ = "checkpoint buffer too small (see dpd_checkpoint_bytes)";
+            return DPD_EINVAL;
+        }
+        int rc = ensure_io((size_t)h.n);   // 72 B per bead: holds either record
+        if (rc) return rc;
+        k_inv_perm<<<blocks(h.n), 256, 0, stream_>>>(h.bead0, h.n, id_[cur_], inv_perm_);
+        k_ckpt_out<P><<<blocks(h.n), 256, 0, stream_>>>(s, sys_, pos_, key_, vel_[cur_],
+                                                          frc_[cur_], inv_perm_,
+                                                          reinterpret_cast<Rec *>(io_));
+        launches_ += 2;
+        DPD_CU(cudaGetLastError());
+        CkptHeader hd;
+        fill_header(h, hd);
+        std::memcpy(buf, &hd, sizeof(hd));
+        DPD_CU(cudaMemcpyAsync(static_cast<char *>(buf) + sizeof(hd), io_,
+                               (size_t)h.n * sizeof(Rec), cudaMemcpyDeviceToHost, stream_));
+        DPD_CU(cudaStreamSynchronize(stream_));
+        return check_status();
+    }
+
+    int set_checkpoint(int s, const void *buf, int64_t bytes) override {
+        if (s < 0 || s >= NS_ || !hs_[s].live || !buf) return DPD_EINVAL;
+        int rc = check_status();
+        if (rc) return rc;
+        SysHost &h = hs_[s];
+        if (bytes < checkpoint_bytes(s)) {
+            err_ = "checkpoint too short for this system";
+            return DPD_EINVAL;
+        }
+        CkptHeader want, got;
+        fill_header(h, want);
+        std::memcpy(&got, buf, sizeof(got));
+        if (std::memcmp(got.magic, want.magic, 8) || got.version != want.version ||
+            got.precision != want.precision || got.n != want.n ||
+            got.record_bytes != want.record_bytes || std::memcmp(got.nc, want.nc, sizeof(got.nc)) ||
+            std::memcmp(got.L, want.L, sizeof(got.L)) || got.seed != want.seed) {
+            err_ = "checkpoint does not belong to a system of this precision, size, box and seed";
+            return DPD_EINVAL;
+        }
+        const Rec *rec = reinterpret_cast<const Rec *>(static_cast<const char *>(buf) + sizeof(got));
+        if (P::kOffsets) {   // keys index the cell counts: check them before the device does
+            for (int i = 0; i < h.n; ++i) {
+                uint32_t k;
+                std::memcpy(&k, reinterpret_cast<const char *>(rec + i), sizeof(k));
+                if (k >= (uint32_t)h.ncell) {
+                    err_ = "checkpoint holds a cell key out of range";
+                    return DPD_EINVAL;
+                }
+            }
+        }
+        if ((rc = ensure_io((size_t)h.n))) return rc;
+        const int old = cur_ ^ 1;
+        InitArgs<P> ia;
+        ia.s = s;
+        ia.sys = sys_;
+        ia.pos_in = ia.vel_in = nullptr;
+        ia.types = types_ + h.bead0;
+        ia.pos_tmp = pos_tmp_;
+        ia.vel = vel_[old];
+        ia.frc = frc_[old];
+        ia.key_tmp = key_tmp_;
+        ia.rank = rank_;
+        ia.count = count_;
+        ia.id = id_[old];
+        ia.status = status_;
+        ia.i0 = 0;
+        ia.i1 = h.n;
+        DPD_CU(cudaMemcpyAsync(io_, rec, (size_t)h.n * sizeof(Rec), cudaMemcpyHostToDevice,
+                               stream_));
+        k_ckpt_in<P><<<blocks(h.n), 256, 0, stream_>>>(ia, reinterpret_cast<const Rec *>(io_));
+        ++launches_;
+        DPD_CU(cudaGetLastError());
+        long long sv = (long long)got.step;
+        DPD_CU(cudaMemcpyAsync(counter_ + s, &sv, sizeof(long long), cudaMemcpyHostToDevice,
+                               stream_));
+        if ((rc = enqueue_sort(h.bead0, h.bead0 + h.n, h.cell0, h.cell0 + h.ncell, old, cur_)))
+            return rc;
+        h.obs_fresh = false;
+        DPD_CU(cudaStreamSynchronize(stream_));
+        int st = 0;
+        DPD_CU(cudaMemcpy(&st, status_, sizeof(int), cudaMemcpyDeviceToHost));
+        if (st & ST_BADINPUT) {
+            st &= ~ST_BADINPUT;
+            DPD_CU(cudaMemcpy(status_, &st, sizeof(int), cudaMemcpyHostToDevice));
+            h.has_state = false;
+            err_ = "checkpoint holds a non-finite value";
+            return DPD_EINVAL;
+        }
+        h.has_state = true;
+        h.step = got.step;
+        return check_status();
+    }
+
     int sync() override {
         DPD_CU(cudaStreamSynchronize(stream_));
         return check_status();
@@ -537,6 +643,21 @@ class BatchEngine : public BatchBase {
         allocs_.push_back(q);
         *p = reinterpret_cast<T *>(q);
         return DPD_OK;
+    }
+
+    void fill_header(const SysHost &h, CkptHeader &hd) const {
+        std::memset(&hd, 0, sizeof(hd));
+        std::memcpy(hd.magic, "DPDCKPT1", 8);
+        hd.version = 1;
+        hd.precision = P::kOffsets ? DPD_FP32 : DPD_FP64;
+        hd.n = h.n;
+        hd.step = h.step;
+        for (int k = 0; k < 3; ++k) {
+            hd.nc[k] = h.cfg.nc[k];
+            hd.L[k] = h.cfg.L[k];
+        }
+        hd.record_bytes = (uint32_t)sizeof(Rec);
+        hd.seed = h.cfg.seed;
     }
 
     // staging for one system's host <-> device copies (9 doubles per bead)

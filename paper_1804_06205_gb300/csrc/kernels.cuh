@@ -665,6 +665,7 @@ struct PairSmem {
         if (!P::kOffsets) b += (size_t)cap * sizeof(float4);      // FP64: their binary32 copies
         b += 2 * PAIR_NR * (size_t)(X + 3) * sizeof(int);          // staged / source cell starts
         b += PAIR_NR * 3 * PAIR_PC * sizeof(int) + 4 * 4 * sizeof(int);   // runs, home rows
+        b += PAIR_NR * sizeof(int);                                // row keys
         b = align16(b);
         b += (size_t)ntmax * ntmax * sizeof(real) + PAIR_NR * 2 * sizeof(real);
         b = align16(b);
@@ -805,7 +806,8 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
     int *s_src = s_cs + PAIR_NR * (la.Xmax + 3);
     int *s_pc = s_src + PAIR_NR * (la.Xmax + 3);
     int *s_hr = s_pc + PAIR_NR * 3 * PAIR_PC;        // home rows: staged row, first, count, global
-    size_t off = PairSmem<P>::align16((size_t)((unsigned char *)(s_hr + 16) - smem));
+    int *s_rkey = s_hr + 16;                         // per staged row: key of its cell x = 0
+    size_t off = PairSmem<P>::align16((size_t)((unsigned char *)(s_rkey + PAIR_NR) - smem));
     real *s_a = reinterpret_cast<real *>(smem + off);
     real *s_rsh = s_a + la.ntmax * la.ntmax;         // per staged row: y, z frame shift
     off = PairSmem<P>::align16((size_t)((unsigned char *)(s_rsh + 2 * PAIR_NR) - smem));
@@ -828,6 +830,99 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
     const int SY = BYe + 2, NRe = SY * (BZe + 2);
     const real hx = a.h[0], hy = a.h[1], hz = a.h[2];
 
+#ifndef DPD_V2
+#define DPD_V2 0
+#endif
+#if DPD_V2
+    for (int e = tid; e < a.ntypes * a.ntypes; e += T) s_a[e] = a.a[e];
+    // The (row, cell) grid of the neighbourhood is shared by all threads; a
+    // thread's position in it advances by T without any division.
+    const int gr0 = tid / W, gk0 = tid - gr0 * W, gdr = T / W, gdk = T - gdr * W;
+    if (tid < NRe) {   // each staged row's first key (wrapped y, z) and frame shift
+        const int r = tid;
+        const int uy = r % SY - 1, uz = r / SY - 1;
+        int yy = y0 + uy, zz = z0 + uz;
+        yy += yy < 0 ? a.ny : (yy >= a.ny ? -a.ny : 0);
+        zz += zz < 0 ? a.nz : (zz >= a.nz ? -a.nz : 0);
+        s_rkey[r] = (int)(((uint32_t)zz * a.ny + yy) * a.nx);
+        real sy, sz;
+        if (P::kOffsets) {       // offset -> brick frame
+            sy = mul_rn((real)uy, hy);
+            sz = mul_rn((real)uz, hz);
+        } else {                 // absolute -> brick frame, undoing the row's wrap
+            sy = mul_rn((real)(uy - yy), hy);
+            sz = mul_rn((real)(uz - zz), hz);
+        }
+        s_rsh[2 * r] = sy;
+        s_rsh[2 * r + 1] = sz;
+    }
+    __syncthreads();
+    // per staged cell: counts (k = 0..Xe+1 <-> ux = -1..Xe), k = Xe+2 is the row end;
+    // the threads share the flattened (row, cell) grid, so that many cell-start
+    // loads are in flight at once
+    {
+        int r = gr0, k = gk0;
+#pragma unroll 2
+        for (int e = tid; e < NRe * W; e += T) {
+            int cnt = 0, first = 0;
+            if (k <= Xe + 1) {
+                int xx = x0 + k - 1;
+                xx += xx < 0 ? a.nx : (xx >= a.nx ? -a.nx : 0);
+                const uint32_t c = (uint32_t)s_rkey[r] + (uint32_t)xx;
+                first = (int)a.cell_start[c];
+                cnt = (int)a.cell_start[c + 1] - first;
+            }
+            s_cs[e] = cnt;
+            s_src[e] = first;
+            k += gdk;
+            r += gdr;
+            if (k >= W) {
+                k -= W;
+                ++r;
+            }
+        }
+    }
+    __syncthreads();
+    if (tid < 32) {   // exclusive scan of the counts: staged start of each cell
+        int carry = 0;
+        const int tot = NRe * W;
+        for (int b = 0; b < tot; b += 32) {
+            const int v = (b + tid < tot) ? s_cs[b + tid] : 0;
+            int inc = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(FULL, inc, o);
+                if (tid >= o) inc += u;
+            }
+            if (b + tid < tot) s_cs[b + tid] = carry + inc - v;
+            carry += __shfl_sync(FULL, inc, 31);
+        }
+    }
+    __syncthreads();
+    if (tid < NRe) {   // contiguous source runs of each staged row, split where x wraps:
+        const int r = tid;   // at k = 1 when x0 = 0, and where x0 + k - 1 = nx
+        const int kw = a.nx - x0 + 1;
+        const bool w1 = x0 == 0, w2 = kw <= Xe + 1;
+        const int kend = Xe + 2;
+        // run j covers cells [kb_j, kb_{j+1}); -1: no such run
+        const int kb1 = w1 ? 1 : (w2 ? kw : kend);
+        const int kb2 = w1 ? (w2 ? kw : kend) : (w2 ? kend : -1);
+        const int kb3 = (w1 && w2) ? kend : -1;
+        auto put = [&](int j, int k0, int k1) {
+            int *pc = s_pc + (r * 3 + j) * PAIR_PC;
+            if (k1 >= 0) {
+                pc[0] = s_src[r * W + k0];                     // first source slot
+                pc[1] = s_cs[r * W + k0];                      // first staged slot
+                pc[2] = s_cs[r * W + k1] - s_cs[r * W + k0];   // length
+            } else {
+                pc[2] = 0;
+            }
+        };
+        put(0, 0, kb1);
+        put(1, kb1, kb2);
+        put(2, kb2, kb3);
+    }
+#else
     for (int e = tid; e < a.ntypes * a.ntypes; e += T) s_a[e] = a.a[e];
     // per staged cell: counts (k = 0..Xe+1 <-> ux = -1..Xe), k = Xe+2 is the row end;
     // the threads share the flattened (row, cell) grid, so that many cell-start
@@ -905,6 +1000,7 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
         }
         for (; np < 3; ++np) s_pc[(r * 3 + np) * PAIR_PC + 2] = 0;
     }
+#endif
     if (tid < 4) {     // home rows (ry, rz) = (tid % 2, tid / 2)
         const int ry = tid % 2, rz = tid / 2;
         int hcount = 0, first = 0, gfirst = 0, sr = 0;
@@ -963,8 +1059,19 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
         }
         // into the brick's frame, cell by cell: x by the cell's place in
         // the brick, y and z by the row's shift
+#if DPD_V2
+        int r = gr0 - gdr, k = gk0 - gdk;
+        for (int e = tid; e < NRe * W; e += T) {
+            k += gdk;
+            r += gdr;
+            if (k >= W) {
+                k -= W;
+                ++r;
+            }
+#else
         for (int e = tid; e < NRe * W; e += T) {
             const int r = e / W, k = e - r * W;
+#endif
             if (k > Xe + 1) continue;                 // the row-end entry
             const int lo = max(s_cs[e], c0), hi = min(s_cs[e + 1], c1);
             if (lo >= hi) continue;
@@ -1159,6 +1266,45 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
                             if (nh > 0) break;                   // evaluate first, resume here
                             qe = q + PAIR_HMAX;                  // a crowded row: part of it
                         }
+#ifndef DPD_V1
+#define DPD_V1 0
+#endif
+#if DPD_V1
+                        {   // queue [level][lane]: the staged slot of each hit.  Every
+                            // candidate is stored at the lane's next free level and the
+                            // level advances on a hit only; a row never holds more
+                            // candidates than free levels, so the stores stay in the queue
+                            int i = q - c0;
+                            const int ie = qe - c0;
+                            uint16_t *qp = my_q + nh * 32 + lane;
+                            for (; i + 1 < ie; i += 2) {   // two at a time
+                                const float4 pa = s_scan[i], pb = s_scan[i + 1];
+                                const float2 da = __fadd2_rn(make_float2(pa.x, pa.y), nxy);
+                                const float2 db = __fadd2_rn(make_float2(pb.x, pb.y), nxy);
+                                const float az = add_rn(pa.z, nzs), bz = add_rn(pb.z, nzs);
+                                const float ra = fma_rn(az, az, fma_rn(da.y, da.y, mul_rn(da.x, da.x)));
+                                const float rb = fma_rn(bz, bz, fma_rn(db.y, db.y, mul_rn(db.x, db.x)));
+                                const bool ha = ra < scan_lim && (P::kOffsets ? ra > 0.0f : i != (int)self);
+                                const bool hb = rb < scan_lim && (P::kOffsets ? rb > 0.0f : i + 1 != (int)self);
+                                *qp = (uint16_t)i;
+                                qp += ha ? 32 : 0;
+                                *qp = (uint16_t)(i + 1);
+                                qp += hb ? 32 : 0;
+                            }
+                            if (i < ie) {
+                                const float4 pj = s_scan[i];
+                                const float2 d = __fadd2_rn(make_float2(pj.x, pj.y), nxy);
+                                const float dzv = add_rn(pj.z, nzs);
+                                const float r2 = fma_rn(dzv, dzv, fma_rn(d.y, d.y, mul_rn(d.x, d.x)));
+                                const bool h = r2 < scan_lim && (P::kOffsets ? r2 > 0.0f : i != (int)self);
+                                *qp = (uint16_t)i;
+                                qp += h ? 32 : 0;
+                                ++i;
+                            }
+                            q = i + c0;
+                            nh = (int)((qp - my_q) >> 5);
+                        }
+#else
                         {   // queue [level][lane]: the staged slot of each hit
                             const float4 *pp = s_scan + (q - c0);
                             uint16_t ent = (uint16_t)(q - c0);
@@ -1193,6 +1339,7 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
                             }
                             nh = (int)((qp - my_q) >> 5);
                         }
+#endif
                         if (q < qe_full) break;
                     }
                     more = r9 < 9;
@@ -1568,6 +1715,85 @@ __global__ void __launch_bounds__(256) k_unpermute(int s, int i0, int i1, const 
     opos[3 * i] = x; opos[3 * i + 1] = y; opos[3 * i + 2] = z;
     ovel[3 * i] = v.x; ovel[3 * i + 1] = v.y; ovel[3 * i + 2] = v.z;
     ofrc[3 * i] = f.x; ofrc[3 * i + 1] = f.y; ofrc[3 * i + 2] = f.z;
+}
+
+// --------------------------------------------------------------------------
+// Checkpoints: the exact state (position representation, v, f) of one system
+// in bead-id order, so that a restored system continues bit for bit.
+// FP32 record: key, offset[3], v[3], f[3] (40 B); FP64: x[3], v[3], f[3] (72 B).
+// --------------------------------------------------------------------------
+struct CkptRec32 {
+    uint32_t key;
+    float o[3], v[3], f[3];
+};
+struct CkptRec64 {
+    double x[3], v[3], f[3];
+};
+template <class P>
+struct CkptRec;
+template <>
+struct CkptRec<PF32> {
+    using type = CkptRec32;
+};
+template <>
+struct CkptRec<PF64> {
+    using type = CkptRec64;
+};
+
+template <class P>
+__global__ void __launch_bounds__(256) k_ckpt_out(int s, const SysDesc<P> *sys,
+                                                  const typename P::vec4 *pos, const uint32_t *key,
+                                                  const typename P::vec4 *vel,
+                                                  const typename P::vec4 *frc,
+                                                  const int32_t *inv_perm,
+                                                  typename CkptRec<P>::type *out) {
+    const SysDesc<P> &D = sys[s];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= D.n) return;
+    const int t = inv_perm[D.bead0 + i];
+    const typename P::vec4 p = pos[t], v = vel[t], f = frc[t];
+    typename CkptRec<P>::type r;
+    if constexpr (P::kOffsets) {
+        r.key = key[t];
+        r.o[0] = p.x; r.o[1] = p.y; r.o[2] = p.z;
+    } else {
+        r.x[0] = p.x; r.x[1] = p.y; r.x[2] = p.z;
+    }
+    r.v[0] = v.x; r.v[1] = v.y; r.v[2] = v.z;
+    r.f[0] = f.x; r.f[1] = f.y; r.f[2] = f.z;
+    out[i] = r;
+}
+
+// Restore: like the initial binning (k_init), from checkpoint records (FP32
+// keys were checked against the cell count on the host).
+template <class P>
+__global__ void __launch_bounds__(256) k_ckpt_in(InitArgs<P> a,
+                                                 const typename CkptRec<P>::type *rec) {
+    using real = typename P::real;
+    const SysDesc<P> &D = a.sys[a.s];
+    const int i = a.i0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.i1) return;
+    const int t = D.bead0 + i;
+    const typename CkptRec<P>::type r = rec[i];
+    typename P::vec4 out;
+    uint32_t key;
+    bool fin = isfinite(r.v[0]) && isfinite(r.v[1]) && isfinite(r.v[2]) && isfinite(r.f[0]) &&
+               isfinite(r.f[1]) && isfinite(r.f[2]);
+    if constexpr (P::kOffsets) {
+        fin = fin && isfinite(r.o[0]) && isfinite(r.o[1]) && isfinite(r.o[2]);
+        key = r.key;
+        out = mk4<typename P::vec4, real>(r.o[0], r.o[1], r.o[2], P::pack_int(a.types[i]));
+    } else {
+        place_bead<P>(D, r.x[0], r.x[1], r.x[2], P::pack_int(a.types[i]), out, key, a.status,
+                      ST_BADINPUT);
+    }
+    if (!fin) atomicOr(a.status, ST_BADINPUT);
+    a.pos_tmp[t] = out;
+    a.key_tmp[t] = key;
+    a.rank[t] = atomicAdd(&a.count[D.cell0 + key], 1u);
+    a.vel[t] = mk4<typename P::vec4, real>(r.v[0], r.v[1], r.v[2], (real)0);
+    a.frc[t] = mk4<typename P::vec4, real>(r.f[0], r.f[1], r.f[2], (real)0);
+    a.id[t] = i;
 }
 
 template <class P>

@@ -36,7 +36,9 @@ EXPORTED = ("dpd_default_options", "dpd_create", "dpd_set_state", "dpd_step", "d
             "dpd_batch_add", "dpd_batch_remove", "dpd_batch_step", "dpd_batch_get_state",
             "dpd_batch_observables", "dpd_batch_usage", "dpd_batch_sync", "dpd_batch_launch_count",
             "dpd_batch_last_error", "dpd_batch_destroy", "dpd_batch_profile_begin",
-            "dpd_batch_profile_end", "dpd_wait_check", "dpd_bm_check")
+            "dpd_batch_profile_end", "dpd_wait_check", "dpd_bm_check", "dpd_checkpoint_bytes",
+            "dpd_get_checkpoint", "dpd_set_checkpoint", "dpd_batch_checkpoint_bytes",
+            "dpd_batch_get_checkpoint", "dpd_batch_set_checkpoint")
 
 
 class dpd_box(C.Structure):
@@ -110,6 +112,12 @@ def _load():
     lib.dpd_wait_check.restype = C.c_int
     lib.dpd_bm_check.argtypes = [P, P]
     lib.dpd_bm_check.restype = C.c_int
+    lib.dpd_checkpoint_bytes.argtypes = [P, P]
+    lib.dpd_get_checkpoint.argtypes = [P, P, C.c_int64]
+    lib.dpd_set_checkpoint.argtypes = [P, P, C.c_int64]
+    lib.dpd_batch_checkpoint_bytes.argtypes = [P, C.c_int32, P]
+    lib.dpd_batch_get_checkpoint.argtypes = [P, C.c_int32, P, C.c_int64]
+    lib.dpd_batch_set_checkpoint.argtypes = [P, C.c_int32, P, C.c_int64]
     lib.dpd_batch_create.argtypes = [P, P, P]
     lib.dpd_batch_add.argtypes = [P, P, C.c_int64, P, C.c_int32, P, C.c_double, C.c_double,
                                   C.c_double, P, C.c_int64, P, C.c_int64, C.c_double, C.c_uint64,
@@ -278,6 +286,18 @@ class System:
                     "dpd_get_cells")
         return key, order, start
 
+    def get_checkpoint(self) -> bytes:
+        """The exact state as an opaque byte string (dpd_get_checkpoint)."""
+        nb = C.c_int64(0)
+        self._check(lib.dpd_checkpoint_bytes(self.h, C.byref(nb)), "dpd_checkpoint_bytes")
+        buf = C.create_string_buffer(nb.value)
+        self._check(lib.dpd_get_checkpoint(self.h, buf, nb.value), "dpd_get_checkpoint")
+        return buf.raw
+
+    def set_checkpoint(self, data: bytes):
+        self._check(lib.dpd_set_checkpoint(self.h, C.c_char_p(data), len(data)),
+                    "dpd_set_checkpoint")
+
     def sync(self):
         self._check(lib.dpd_sync(self.h), "dpd_sync")
 
@@ -392,6 +412,19 @@ class Batch:
         self._check(lib.dpd_batch_observables(self.h, int(s), C.byref(o)),
                     "dpd_batch_observables")
         return o.as_dict()
+
+    def get_checkpoint(self, s) -> bytes:
+        nb = C.c_int64(0)
+        self._check(lib.dpd_batch_checkpoint_bytes(self.h, int(s), C.byref(nb)),
+                    "dpd_batch_checkpoint_bytes")
+        buf = C.create_string_buffer(nb.value)
+        self._check(lib.dpd_batch_get_checkpoint(self.h, int(s), buf, nb.value),
+                    "dpd_batch_get_checkpoint")
+        return buf.raw
+
+    def set_checkpoint(self, s, data: bytes):
+        self._check(lib.dpd_batch_set_checkpoint(self.h, int(s), C.c_char_p(data), len(data)),
+                    "dpd_batch_set_checkpoint")
 
     def usage(self):
         used = np.zeros(4, np.int64)

@@ -69,3 +69,25 @@ def test_wait_check_rejects_bad_arguments(binding):
     # argument checks come before any CUDA call
     assert binding.wait_check(True, tries=0) == binding.DPD_EINVAL
     assert binding.wait_check(True, tries=binding.WAIT_CHECK_MAX_TRIES + 1) == binding.DPD_EINVAL
+
+
+def test_noalloc_rejects_overflowing_boxes_before_touching_memory(binding):
+    # host-side checks: the pointers are never dereferenced for these sizes
+    fake = 0x1000
+    big = float(binding.NOALLOC_MAX_CELLS)
+    for L in ((big, big, big), (big + 1.0, 3.0, 3.0), (2048.0, 2048.0, 2048.0),
+              (1e300, 3.0, 3.0), (float("inf"), 3.0, 3.0), (float("nan"), 3.0, 3.0)):
+        assert binding.cells_noalloc(fake, 10, L, fake, fake, fake) == binding.DPD_EINVAL, L
+    assert binding.cells_noalloc(fake, binding.NOALLOC_MAX_N + 1, 50.0, fake, fake,
+                                 fake) == binding.DPD_EINVAL
+    assert binding.cells_noalloc(fake, 0, 50.0, fake, fake, fake) == binding.DPD_EINVAL
+
+
+@pytest.mark.parametrize("L", [(4194304.0, 4194304.0, 4194304.0), (2.0 ** 31, 3.0, 3.0),
+                               (1e10, 1e10, 1e10), (65536.0, 65536.0, 3.0)])
+def test_create_rejects_boxes_with_too_many_cells(binding, L):
+    # rejected while validating the box, before any device allocation
+    with pytest.raises(binding.DPDError) as e:
+        binding.System(L, np.zeros(4, np.int32), np.array([[25.0]]), 4.5, 1.0, 0.04)
+    assert e.value.code == binding.DPD_EINVAL
+    assert "too many cells" in str(e.value)
