@@ -90,6 +90,13 @@ typedef struct {
     int32_t tile_cells;   /* pair-kernel home cells per block (0 = auto)     */
     int32_t threads;      /* pair-kernel threads per block (0 = auto)        */
     int32_t use_graph;    /* replay steps from captured CUDA graphs (0)      */
+    int32_t persistent;   /* 1: each dpd_step / dpd_batch_step call is ONE
+                             cooperative launch in which resident blocks run
+                             every phase of every step, with bounded grid-wide
+                             barriers between phases (0: one launch per kernel
+                             per step).  Same bits either way.  Ignored when
+                             running means are sampled or graphs are used.   */
+    int32_t pad;          /* ignored                                         */
     void *cuda_stream;    /* cudaStream_t to run on; NULL = own stream       */
 } dpd_options;
 
@@ -112,7 +119,8 @@ typedef struct {
 } dpd_obs;
 
 /* Fill *opt with the defaults (lambda 0.65, seed 0, FP32, Gaussian noise,
- * sample_every 0, automatic tiles, direct launches, own stream).  Direct
+ * sample_every 0, automatic tiles, direct launches, not persistent, own
+ * stream).  Direct
  * launches use programmatic dependent launch, so each kernel of a step is
  * scheduled while the previous one drains; replaying captured CUDA graphs
  * (use_graph = 1) gives the same bits. */
@@ -252,6 +260,19 @@ int dpd_destroy(dpd_handle *h);
  * DPD_ECUDA if a CUDA call fails. */
 #define DPD_WAIT_CHECK_MAX_TRIES (1 << 22)
 int dpd_wait_check(int32_t deliver, int32_t tries, void *cuda_stream);
+
+/* Check of the failure detection on the grid-wide barrier of the persistent
+ * step kernel (dpd_options.persistent), without a fault.  A cooperative grid of
+ * 4 blocks meets at one barrier; complete != 0: the barrier expects the 4 blocks
+ * and completes, the call returns DPD_OK; complete == 0: it expects a fifth
+ * block that does not exist, so every block waits out `budget_cycles` clock
+ * cycles (its clock64() budget), records the timeout and leaves, and the call
+ * returns DPD_ETIMEOUT; the CUDA context stays usable.  budget_cycles in
+ * [1, DPD_GRID_WAIT_CHECK_MAX_CYCLES] (else DPD_EINVAL); cuda_stream: NULL = the
+ * legacy default stream.  Allocates nothing; synchronises the stream;
+ * DPD_ECUDA if a CUDA call fails. */
+#define DPD_GRID_WAIT_CHECK_MAX_CYCLES 4000000000LL
+int dpd_grid_wait_check(int32_t complete, int64_t budget_cycles, void *cuda_stream);
 
 /* Check of the FP64 path's Box-Muller functions of the uniforms u = n 2^-24
  * (n odd): the table-driven ln u (after P. T. P. Tang, ACM TOMS 16, 1990) and

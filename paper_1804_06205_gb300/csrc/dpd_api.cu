@@ -155,6 +155,7 @@ void dpd_default_options(dpd_options *opt) {
     opt->tile_cells = 0;
     opt->threads = 0;
     opt->use_graph = 0;
+    opt->persistent = 0;
     opt->cuda_stream = nullptr;
 }
 
@@ -188,6 +189,7 @@ int dpd_create(const dpd_box *box, int64_t n, const int32_t *types, int32_t ntyp
     bc.threads = o.threads;
     bc.sample_every = o.sample_every < 0 ? 0 : o.sample_every;
     bc.use_graph = o.use_graph != 0;
+    bc.persistent = o.persistent != 0;
     bc.stream = o.cuda_stream;
     dpd_handle *h = new (std::nothrow) dpd_handle();
     if (!h) return DPD_ENOMEM;
@@ -336,6 +338,7 @@ int dpd_batch_create(const dpd_batch_capacity *cap, const dpd_options *opt, dpd_
     bc.threads = b->opt.threads;
     bc.sample_every = 0;
     bc.use_graph = b->opt.use_graph != 0;
+    bc.persistent = b->opt.persistent != 0;
     bc.stream = b->opt.cuda_stream;
     int rc = DPD_OK;
     std::string err;

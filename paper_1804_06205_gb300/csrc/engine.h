@@ -52,6 +52,7 @@ struct BatchConfig {
     int32_t threads;                 // pair-kernel threads per block (0 = auto)
     int32_t sample_every;            // running means every k steps (0 = off)
     bool use_graph;
+    bool persistent;                 // one cooperative launch per dpd_step call
     void *stream;                    // cudaStream_t or nullptr
 };
 

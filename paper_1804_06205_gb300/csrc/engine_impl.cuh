@@ -13,6 +13,7 @@
 #include <memory>
 
 #include "kernels.cuh"
+#include "persist.cuh"
 
 namespace dpd {
 
@@ -123,7 +124,7 @@ class BatchEngine : public BatchBase {
             (rc = alloc(&bpar_, (size_t)NBD_)) || (rc = alloc(&rmap_, (size_t)NRB_)) ||
             (rc = alloc(&rsys_, (size_t)NS_)) || (rc = alloc(&partial_, (size_t)NRB_ * RED_K)) ||
             (rc = alloc(&obs_, (size_t)NS_ * RED_K)) || (rc = alloc(&acc_, (size_t)NS_ * 4)) ||
-            (rc = alloc(&old_bead0_, (size_t)NS_)))
+            (rc = alloc(&old_bead0_, (size_t)NS_)) || (rc = alloc(&bar_, 1)))
             return rc;
         if (!P::kOffsets) {   // FP64 Box-Muller logarithm tables
             if ((rc = alloc(&lntab_, 1))) return rc;
@@ -318,6 +319,15 @@ class BatchEngine : public BatchBase {
             if (!hs_[k].has_state) return DPD_ENOSTATE;
         int rc = peek_status();
         if (rc) return rc;
+        if (nsteps > 0 && bc_.persistent && bc_.sample_every == 0 && !bc_.use_graph &&
+            persist_grid_ > 0) {
+            if ((rc = launch_persistent(nsteps))) return rc;
+            for (int s : order_) {
+                hs_[s].step += nsteps;
+                hs_[s].obs_fresh = false;
+            }
+            return DPD_OK;
+        }
         // Step kinds: 0 plain, its bond kernel also doing the next step's position
         // update (which that step then skips); 1 plain without it, the last step of
         // a call; 2 sampled for the running means.  Observables are otherwise
@@ -567,7 +577,8 @@ class BatchEngine : public BatchBase {
         long long sv = (long long)got.step;
         DPD_CU(cudaMemcpyAsync(counter_ + s, &sv, sizeof(long long), cudaMemcpyHostToDevice,
                                stream_));
-        if ((rc = enqueue_sort(h.bead0, h.bead0 + h.n, h.cell0, h.cell0 + h.ncell, old, cur_)))
+        if ((rc = enqueue_sort(h.bead0, h.bead0 + h.n, h.cell0, h.cell0 + h.ncell, old, cur_,
+                               true)))
             return rc;
         h.obs_fresh = false;
         DPD_CU(cudaStreamSynchronize(stream_));
@@ -680,6 +691,10 @@ class BatchEngine : public BatchBase {
     }
 
     static int blocks(int n, int t = 256) { return std::max(1, (n + t - 1) / t); }
+
+    // the only resident system when there is one (its kernels then need no
+    // bead -> system map), else -1
+    int sys1() const { return order_.size() == 1 ? order_[0] : -1; }
 
     // chunks of a host <-> device state transfer: at least IO_CHUNK beads each
     static int io_chunks(int n) { return std::max(1, std::min(IO_MAXCH, n / IO_CHUNK)); }
@@ -863,6 +878,14 @@ class BatchEngine : public BatchBase {
         smem_ = PairSmem<P>::bytes(capmax_, xmax_, T_, ntmax_, true);
         smem_n_ = PairSmem<P>::bytes(capmax_, xmax_, T_, ntmax_, false);
         int rc;
+        if (bc_.persistent) {
+            switch (T_) {
+                case 64: rc = set_persist_t<64>(); break;
+                case 256: rc = set_persist_t<256>(); break;
+                default: rc = set_persist_t<128>(); break;
+            }
+            if (rc) return rc;
+        }
         switch (T_) {
             case 64:
                 if ((rc = set_pair_smem_t<64, true>())) return rc;
@@ -886,6 +909,169 @@ class BatchEngine : public BatchBase {
         if ((size_t)fa.maxDynamicSharedSizeBytes >= need) return DPD_OK;
         DPD_CU(cudaFuncSetAttribute(k_pair<P, T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)need));
+        return DPD_OK;
+    }
+
+    // Shared memory of the persistent step kernel (the plain pair kernel's) and
+    // its co-resident grid: every block must be resident at once.
+    template <int T>
+    int set_persist_t() {
+        persist_grid_ = 0;
+        if (smem_n_ > 48 * 1024) {
+            cudaFuncAttributes fa;
+            DPD_CU(cudaFuncGetAttributes(&fa, k_steps<P, T>));
+            if ((size_t)fa.maxDynamicSharedSizeBytes < smem_n_)
+                DPD_CU(cudaFuncSetAttribute(k_steps<P, T>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem_n_));
+        }
+        int dev = 0, nsm = 0, per_sm = 0;
+        DPD_CU(cudaGetDevice(&dev));
+        DPD_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        DPD_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_steps<P, T>, T, smem_n_));
+        persist_grid_ = per_sm * nsm;
+        return DPD_OK;
+    }
+
+    template <int T>
+    int launch_persistent_t(const StepArgs<P> &sa) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)persist_grid_);
+        cfg.blockDim = dim3((unsigned)T);
+        cfg.dynamicSmemBytes = smem_n_;
+        cfg.stream = stream_;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        DPD_CU(cudaLaunchKernelEx(&cfg, k_steps<P, T>, sa));
+        ++launches_;
+        return DPD_OK;
+    }
+
+    // All steps of one dpd_step call in one cooperative launch (persist.cuh);
+    // the kernel runs the same phases in the same order as enqueue_step.
+    int launch_persistent(int64_t nsteps) {
+        StepArgs<P> sa;
+        std::memset(&sa, 0, sizeof(sa));
+        sa.nsteps = (int)nsteps;
+        sa.nbeads = used_beads_;
+        sa.ncells = used_cells_;
+        sa.nbricks = used_bricks_;
+        sa.ntiles = (used_cells_ + SCAN_B - 1) / SCAN_B;
+        sa.with_update = 1;
+        UpdArgs<P> &ua = sa.upd;
+        ua.b_lo = 0;
+        ua.b_hi = used_beads_;
+        ua.sys = sys_;
+        ua.bsys = bsys_;
+        ua.sys1 = sys1();
+        ua.key = key_;
+        ua.pos = pos_;
+        ua.vel = vel_[cur_];
+        ua.frc = frc_[cur_];
+        ua.pos_tmp = pos_tmp_;
+        ua.key_tmp = key_tmp_;
+        ua.rank = rank_;
+        ua.count = count_;
+        ua.counter = counter_;
+        ua.status = status_;
+        for (int p = 0; p < 2; ++p) {
+            const int old = cur_ ^ p, nxt = old ^ 1;
+            ScatterArgs<P> &sc = sa.sc[p];
+            sc.b_lo = 0;
+            sc.b_hi = used_beads_;
+            sc.sys = sys_;
+            sc.bsys = bsys_;
+            sc.sys1 = sys1();
+            sc.key_tmp = key_tmp_;
+            sc.rank = rank_;
+            sc.cell_start = cell_start_;
+            sc.id_old = id_[old];
+            sc.src = src_;
+            sc.sid = sid_;
+            GatherArgs<P> &ga = sa.ga[p];
+            ga.b_lo = 0;
+            ga.b_hi = used_beads_;
+            ga.sys = sys_;
+            ga.bsys = bsys_;
+            ga.src = src_;
+            ga.cell_start = cell_start_;
+            ga.sid = sid_;
+            ga.pos_tmp = pos_tmp_;
+            ga.vel_old = vel_[old];
+            ga.frc_old = frc_[old];
+            ga.key_tmp = key_tmp_;
+            ga.pos = pos_;
+            ga.vel = vel_[nxt];
+            ga.frc = frc_[nxt];
+            ga.vt = vt_;
+            ga.key = key_;
+            ga.id = id_[nxt];
+            ga.inv_perm = used_bonds_ > 0 ? inv_perm_ : nullptr;
+            ga.sys1 = sys1();
+            ga.from = rank_;
+            BondArgs<P> &ba = sa.bo[p];
+            ba.b_lo = 0;
+            ba.b_hi = used_beads_;
+            ba.sys = sys_;
+            ba.bsys = bsys_;
+            ba.fpair = fpair_;
+            ba.pos = pos_;
+            ba.key = key_;
+            ba.id = id_[nxt];
+            ba.inv_perm = inv_perm_;
+            ba.bptr = used_bonds_ > 0 ? bptr_ : nullptr;
+            ba.bpartner = bpartner_;
+            ba.bpar = bpar_;
+            ba.sys1 = sys1();
+            ba.from = rank_;
+            ba.vel_old = vel_[old];
+            ba.frc_old = frc_[old];
+            ba.vel = vel_[nxt];
+            ba.frc = frc_[nxt];
+            ba.ev = ev_;
+            ba.pos_tmp = pos_tmp_;
+            ba.key_tmp = key_tmp_;
+            ba.rank = rank_;
+            ba.count = count_;
+            ba.counter = counter_;
+            ba.status = status_;
+        }
+        PairLaunch<P> &pl = sa.pl;
+        pl.sys = sys_;
+        pl.brick_sys = brick_sys_;
+        pl.br_lo = 0;
+        pl.capmax = capmax_;
+        pl.Xmax = xmax_;
+        pl.ntmax = ntmax_;
+        pl.lntab = lntab_;
+        pl.pos = pos_;
+        pl.vt = vt_;
+        pl.key = key_;
+        pl.cell_start = cell_start_;
+        pl.fpair = fpair_;
+        pl.ev = ev_;
+        pl.atab = atab_;
+        pl.counter = counter_;
+        pl.status = status_;
+        sa.count = count_;
+        sa.bsum = bsum_;
+        sa.cell_start = cell_start_;
+        sa.bar = bar_;
+        sa.budget = kBarrierBudget;
+        sa.status = status_;
+        DPD_CU(cudaMemsetAsync(bar_, 0, sizeof(GridBar), stream_));
+        int rc;
+        switch (T_) {
+            case 64: rc = launch_persistent_t<64>(sa); break;
+            case 256: rc = launch_persistent_t<256>(sa); break;
+            default: rc = launch_persistent_t<128>(sa); break;
+        }
+        if (rc) return rc;
+        DPD_CU(cudaGetLastError());
+        if (nsteps & 1) cur_ ^= 1;
         return DPD_OK;
     }
 
@@ -928,7 +1114,8 @@ class BatchEngine : public BatchBase {
 
     // cell division of beads [b_lo, b_hi) / cells [c_lo, c_hi), from the
     // `old` velocity/force/id buffers into the `nxt` ones
-    int enqueue_sort(int b_lo, int b_hi, int c_lo, int c_hi, int old, int nxt) {
+    int enqueue_sort(int b_lo, int b_hi, int c_lo, int c_hi, int old, int nxt,
+                     bool move_vf = false) {
         const int C = c_hi - c_lo, nb = (C + SCAN_B - 1) / SCAN_B;
         DPD_CU(launch_pdl(k_scan1, nb, SCAN_T, 0, stream_, count_ + c_lo, C, bsum_));
         DPD_CU(launch_pdl(k_scan3b, nb, SCAN_T, 0, stream_, count_ + c_lo, C,
@@ -938,6 +1125,7 @@ class BatchEngine : public BatchBase {
         sa.b_hi = b_hi;
         sa.sys = sys_;
         sa.bsys = bsys_;
+        sa.sys1 = sys1();
         sa.key_tmp = key_tmp_;
         sa.rank = rank_;
         sa.cell_start = cell_start_;
@@ -964,7 +1152,10 @@ class BatchEngine : public BatchBase {
         ga.key = key_;
         ga.id = id_[nxt];
         ga.inv_perm = used_bonds_ > 0 ? inv_perm_ : nullptr;
-        DPD_CU(launch_pdl(k_gather<P>, blocks(b_hi - b_lo), 256, 0, stream_, ga));
+        ga.sys1 = sys1();
+        ga.from = rank_;   // the arrival ranks are consumed by the scatter
+        if (move_vf) DPD_CU(launch_pdl(k_gather<P, true>, blocks(b_hi - b_lo), 256, 0, stream_, ga));
+        else DPD_CU(launch_pdl(k_gather<P, false>, blocks(b_hi - b_lo), 256, 0, stream_, ga));
         launches_ += 4;
         DPD_CU(cudaGetLastError());
         return DPD_OK;
@@ -983,9 +1174,13 @@ class BatchEngine : public BatchBase {
         ba.key = key_;
         ba.id = id_[cur_];
         ba.inv_perm = inv_perm_;
-        ba.bptr = bptr_;
+        ba.bptr = used_bonds_ > 0 ? bptr_ : nullptr;
         ba.bpartner = bpartner_;
         ba.bpar = bpar_;
+        ba.sys1 = sys1();
+        ba.from = rank_;                  // source slots recorded by the sort's gather
+        ba.vel_old = vel_[cur_ ^ 1];
+        ba.frc_old = frc_[cur_ ^ 1];
         ba.vel = vel_[cur_];
         ba.frc = frc_[cur_];
         ba.ev = ev_;
@@ -1036,6 +1231,7 @@ class BatchEngine : public BatchBase {
         ua.b_hi = used_beads_;
         ua.sys = sys_;
         ua.bsys = bsys_;
+        ua.sys1 = sys1();
         ua.key = key_;
         ua.pos = pos_;
         ua.vel = vel_[cur_];
@@ -1197,6 +1393,11 @@ class BatchEngine : public BatchBase {
     real *atab_ = nullptr;
     int32_t *bptr_ = nullptr, *bpartner_ = nullptr;
     vec4 *bpar_ = nullptr;
+    GridBar *bar_ = nullptr;               // the persistent kernel's grid barrier
+    int persist_grid_ = 0;                 // its co-resident grid (0: not available)
+    // clock cycles a block of the persistent kernel waits at one grid barrier
+    // before it gives up (about two seconds at 2 GHz)
+    static constexpr long long kBarrierBudget = 4000000000LL;
     int2 *rmap_ = nullptr;
     int4 *rsys_ = nullptr;
     double *partial_ = nullptr, *obs_ = nullptr, *acc_ = nullptr, *io_ = nullptr;

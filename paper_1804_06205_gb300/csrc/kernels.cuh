@@ -358,6 +358,7 @@ struct UpdArgs {
     int b_lo, b_hi;
     const SysDesc<P> *sys;
     const int *bsys;
+    int sys1;                        // the only system of a batch of one, else -1
     const uint32_t *key;             // local cell keys
     const vec4 *pos, *vel, *frc;
     vec4 *pos_tmp;
@@ -366,12 +367,15 @@ struct UpdArgs {
     int *status;
 };
 
+// The system of bead t: a batch of one system needs no map.
+template <class A>
+__device__ __forceinline__ int bead_sys(const A &a, int t) {
+    return a.sys1 >= 0 ? a.sys1 : a.bsys[t];
+}
+
 template <class P>
-__global__ void __launch_bounds__(256) k_update(UpdArgs<P> a) {
-    griddep_wait();
-    const int t = a.b_lo + blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.b_hi) return;
-    const int s = a.bsys[t];
+__device__ __forceinline__ void update_one(const UpdArgs<P> &a, int t) {
+    const int s = bead_sys(a, t);
     const SysDesc<P> &D = a.sys[s];
     if (t == D.bead0) a.counter[s] += 1;   // evaluation counter of this step's force
     typename P::vec4 out;
@@ -380,6 +384,13 @@ __global__ void __launch_bounds__(256) k_update(UpdArgs<P> a) {
     a.pos_tmp[t] = out;
     a.key_tmp[t] = key;
     a.rank[t] = atomicAdd(&a.count[D.cell0 + key], 1u);
+}
+
+template <class P>
+__global__ void __launch_bounds__(256) k_update(UpdArgs<P> a) {
+    griddep_wait();
+    const int t = a.b_lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < a.b_hi) update_one<P>(a, t);
 }
 
 // set_state of one system: host positions/velocities in bead-id order
@@ -522,6 +533,7 @@ struct ScatterArgs {
     int b_lo, b_hi;
     const SysDesc<P> *sys;
     const int *bsys;
+    int sys1;                        // the only system of a batch of one, else -1
     const uint32_t *key_tmp, *rank, *cell_start;
     const int32_t *id_old;
     uint32_t *src;
@@ -529,14 +541,18 @@ struct ScatterArgs {
 };
 
 template <class P>
-__global__ void __launch_bounds__(256) k_scatter(ScatterArgs<P> a) {
-    griddep_wait();
-    const int t = a.b_lo + blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.b_hi) return;
-    const int s = a.bsys[t];
+__device__ __forceinline__ void scatter_one(const ScatterArgs<P> &a, int t) {
+    const int s = bead_sys(a, t);
     const uint32_t slot = a.cell_start[a.sys[s].cell0 + a.key_tmp[t]] + a.rank[t];
     a.src[slot] = (uint32_t)t;
     a.sid[slot] = a.id_old[t];
+}
+
+template <class P>
+__global__ void __launch_bounds__(256) k_scatter(ScatterArgs<P> a) {
+    griddep_wait();
+    const int t = a.b_lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < a.b_hi) scatter_one<P>(a, t);
 }
 
 template <class P>
@@ -545,6 +561,7 @@ struct GatherArgs {
     int b_lo, b_hi;
     const SysDesc<P> *sys;
     const int *bsys;
+    int sys1;                        // the only system of a batch of one, else -1
     const uint32_t *src, *cell_start;
     const int32_t *sid;
     const vec4 *pos_tmp, *vel_old, *frc_old;
@@ -552,17 +569,18 @@ struct GatherArgs {
     vec4 *pos, *vel, *frc, *vt;
     uint32_t *key;
     int32_t *id, *inv_perm;          // inv_perm: null when no system has bonds
+    uint32_t *from;                  // source slot of every new slot (null: not kept)
 };
 
 // Atomic ranks put the beads of a cell in arrival order.  Each arrival finds
 // its canonical place, the cell's start plus the number of the cell's beads
 // with a smaller id (cells hold ~3 beads), and moves its state there.
-template <class P>
-__global__ void __launch_bounds__(256) k_gather(GatherArgs<P> a) {
-    griddep_wait();
-    const int t = a.b_lo + blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.b_hi) return;
-    const SysDesc<P> &D = a.sys[a.bsys[t]];
+// MOVE_VF: also move v and f into the new order (set_state and checkpoint
+// restores); a step leaves them in the old order, where the bond/velocity
+// kernel reads them through the source slot.
+template <class P, bool MOVE_VF>
+__device__ __forceinline__ void gather_one(const GatherArgs<P> &a, int t) {
+    const SysDesc<P> &D = a.sys[bead_sys(a, t)];
     const uint32_t s = a.src[t];
     const int32_t i = a.sid[t];
     const uint32_t k = a.key_tmp[s];
@@ -574,13 +592,23 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs<P> a) {
     const typename P::real lam_dt = D.lam_dt;
     a.pos[u] = a.pos_tmp[s];
     a.key[u] = k;
-    a.vel[u] = v;
-    a.frc[u] = f;
+    if (MOVE_VF) {
+        a.vel[u] = v;
+        a.frc[u] = f;
+    }
+    if (a.from) a.from[u] = s;
     a.id[u] = i;
     if (a.inv_perm) a.inv_perm[D.bead0 + i] = u;
     // Fig. 1 step 2: velocity predictor used by the dissipative force
     a.vt[u] = mk4<typename P::vec4, typename P::real>(v.x + lam_dt * f.x, v.y + lam_dt * f.y,
                                                       v.z + lam_dt * f.z, P::pack_int(i));
+}
+
+template <class P, bool MOVE_VF>
+__global__ void __launch_bounds__(256) k_gather(GatherArgs<P> a) {
+    griddep_wait();
+    const int t = a.b_lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < a.b_hi) gather_one<P, MOVE_VF>(a, t);
 }
 
 // --------------------------------------------------------------------------
@@ -685,6 +713,20 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
 __device__ __forceinline__ void mbar_init(uint64_t *m, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
 }
+// Shared-memory accesses by 32-bit shared-window address (the scan loop).
+__device__ __forceinline__ float4 lds128(uint32_t a) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts16(uint32_t a, uint32_t v) {
+    asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(uint64_t *m) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(m)) : "memory");
+}
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -756,16 +798,18 @@ __device__ __forceinline__ double theta_pair(uint2 x, int noise, double, const L
     return theta_of(x, noise, lt);
 }
 
-template <class P, int T, bool SAMPLE>
-__global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) k_pair(PairLaunch<P> la) {
-    griddep_wait();
+// One block computes the pair forces of the home beads of one brick (T threads).
+// Returns false (in every thread) if a staging copy never completed.  REUSE:
+// the block goes on to another brick, so the staging mbarrier is invalidated
+// at the end (it is initialised again at the start of the next brick).
+template <class P, int T, bool SAMPLE, bool REUSE = false>
+__device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int brick) {
     using real = typename P::real;
     using vec4 = typename P::vec4;
     constexpr int NW = T / 32;
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(32) unsigned char smem[];
     // this block's brick and system
-    const int brick = la.br_lo + blockIdx.x;
     const int sysi = la.brick_sys[brick];
     const SysDesc<P> &D = la.sys[sysi];
     PairArgs<P> a;
@@ -830,10 +874,6 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
     const int SY = BYe + 2, NRe = SY * (BZe + 2);
     const real hx = a.h[0], hy = a.h[1], hz = a.h[2];
 
-#ifndef DPD_V2
-#define DPD_V2 0
-#endif
-#if DPD_V2
     for (int e = tid; e < a.ntypes * a.ntypes; e += T) s_a[e] = a.a[e];
     // The (row, cell) grid of the neighbourhood is shared by all threads; a
     // thread's position in it advances by T without any division.
@@ -922,85 +962,6 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
         put(1, kb1, kb2);
         put(2, kb2, kb3);
     }
-#else
-    for (int e = tid; e < a.ntypes * a.ntypes; e += T) s_a[e] = a.a[e];
-    // per staged cell: counts (k = 0..Xe+1 <-> ux = -1..Xe), k = Xe+2 is the row end;
-    // the threads share the flattened (row, cell) grid, so that many cell-start
-    // loads are in flight at once
-#pragma unroll 2
-    for (int e = tid; e < NRe * W; e += T) {
-        const int r = e / W, k = e - r * W;
-        int cnt = 0, first = 0;
-        if (k <= Xe + 1) {
-            const int uy = r % SY - 1, uz = r / SY - 1;
-            int yy = y0 + uy, zz = z0 + uz, xx = x0 + k - 1;
-            yy += yy < 0 ? a.ny : (yy >= a.ny ? -a.ny : 0);
-            zz += zz < 0 ? a.nz : (zz >= a.nz ? -a.nz : 0);
-            xx += xx < 0 ? a.nx : (xx >= a.nx ? -a.nx : 0);
-            const uint32_t c = ((uint32_t)zz * a.ny + yy) * a.nx + xx;
-            first = (int)a.cell_start[c];
-            cnt = (int)a.cell_start[c + 1] - first;
-        }
-        s_cs[e] = cnt;
-        s_src[e] = first;
-    }
-    if (tid < NRe) {   // each staged row's frame shift
-        const int r = tid;
-        const int uy = r % SY - 1, uz = r / SY - 1;
-        int yy = y0 + uy, zz = z0 + uz;
-        yy += yy < 0 ? a.ny : (yy >= a.ny ? -a.ny : 0);
-        zz += zz < 0 ? a.nz : (zz >= a.nz ? -a.nz : 0);
-        real sy, sz;
-        if (P::kOffsets) {       // offset -> brick frame
-            sy = mul_rn((real)uy, hy);
-            sz = mul_rn((real)uz, hz);
-        } else {                 // absolute -> brick frame, undoing the row's wrap
-            sy = mul_rn((real)(uy - yy), hy);
-            sz = mul_rn((real)(uz - zz), hz);
-        }
-        s_rsh[2 * r] = sy;
-        s_rsh[2 * r + 1] = sz;
-    }
-    __syncthreads();
-    if (tid < 32) {   // exclusive scan of the counts: staged start of each cell
-        int carry = 0;
-        const int tot = NRe * W;
-        for (int b = 0; b < tot; b += 32) {
-            const int v = (b + tid < tot) ? s_cs[b + tid] : 0;
-            int inc = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int u = __shfl_up_sync(FULL, inc, o);
-                if (tid >= o) inc += u;
-            }
-            if (b + tid < tot) s_cs[b + tid] = carry + inc - v;
-            carry += __shfl_sync(FULL, inc, 31);
-        }
-    }
-    __syncthreads();
-    if (tid < NRe) {   // contiguous source runs of each staged row (split at x wraps)
-        const int r = tid;
-        const int uy = r % SY - 1, uz = r / SY - 1;
-        int yy = y0 + uy, zz = z0 + uz;
-        yy += yy < 0 ? a.ny : (yy >= a.ny ? -a.ny : 0);
-        zz += zz < 0 ? a.nz : (zz >= a.nz ? -a.nz : 0);
-        const uint32_t rowkey = ((uint32_t)zz * a.ny + yy) * a.nx;
-        int np = 0, kfirst = 0;
-        for (int k = 1; k <= Xe + 2; ++k) {
-            int xk = x0 + k - 1;
-            xk += xk >= a.nx ? -a.nx : 0;
-            if (k == Xe + 2 || xk == 0) {
-                int *pc = s_pc + (r * 3 + np) * PAIR_PC;
-                pc[0] = s_src[r * W + kfirst];                     // first source slot
-                pc[1] = s_cs[r * W + kfirst];                      // first staged slot
-                pc[2] = s_cs[r * W + k] - s_cs[r * W + kfirst];    // length
-                ++np;
-                kfirst = k;
-            }
-        }
-        for (; np < 3; ++np) s_pc[(r * 3 + np) * PAIR_PC + 2] = 0;
-    }
-#endif
     if (tid < 4) {     // home rows (ry, rz) = (tid % 2, tid / 2)
         const int ry = tid % 2, rz = tid / 2;
         int hcount = 0, first = 0, gfirst = 0, sr = 0;
@@ -1059,7 +1020,6 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
         }
         // into the brick's frame, cell by cell: x by the cell's place in
         // the brick, y and z by the row's shift
-#if DPD_V2
         int r = gr0 - gdr, k = gk0 - gdk;
         for (int e = tid; e < NRe * W; e += T) {
             k += gdk;
@@ -1068,10 +1028,6 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
                 k -= W;
                 ++r;
             }
-#else
-        for (int e = tid; e < NRe * W; e += T) {
-            const int r = e / W, k = e - r * W;
-#endif
             if (k > Xe + 1) continue;                 // the row-end entry
             const int lo = max(s_cs[e], c0), hi = min(s_cs[e + 1], c1);
             if (lo >= hi) continue;
@@ -1117,7 +1073,7 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
         const vec4 pr = a.pos[g], hv = a.vt[g];
         const uint32_t kg = a.key[g];
         if (staged_lo != 0) {
-            if (!stage(0, min(S, cap))) return;
+            if (!stage(0, min(S, cap))) return false;
             staged_lo = 0;
         }
         int uxi = 0;
@@ -1234,7 +1190,7 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
         for (int c0 = 0; c0 < S; c0 += cap) {
             const int c1 = min(S, c0 + cap);
             if (staged_lo != c0) {
-                if (!stage(c0, c1)) return;
+                if (!stage(c0, c1)) return false;
                 staged_lo = c0;
             }
             __syncwarp();
@@ -1242,15 +1198,22 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
             // difference, same r^2), x and y in one packed binary32 add
             const float2 nxy = make_float2(-(float)hp.x, -(float)hp.y);
             const float nzs = -(float)hp.z;
-            const uint16_t self =
-                (self_abs >= c0 && self_abs < c1) ? (uint16_t)(self_abs - c0) : (uint16_t)0xFFFF;
+            const uint32_t self =
+                (self_abs >= c0 && self_abs < c1) ? (uint32_t)(self_abs - c0) : 0xFFFFu;
+            const uint32_t scan_u32 = smem_u32(s_scan), myq_u32 = smem_u32(my_q + lane);
             int r9 = 0, q = 0;
             bool more = active;
             // ---- scan: up to PAIR_HMAX hits, rows (dz, dy) ascending, slots ascending
             auto scan = [&](int &nh) {
                 if (more) {
-                    for (; r9 < 9; ++r9) {
-                        const int dy = r9 % 3 - 1, dz = r9 / 3 - 1;
+                    // the 9 rows unrolled (row offsets and face distances known at
+                    // compile time); a pass resumes at row r9
+                    bool stopped = false;
+#pragma unroll(P::kOffsets ? 9 : 1)
+                    for (int rr = 0; rr < 9; ++rr) {
+                        if (rr < r9) continue;
+                        r9 = rr;
+                        const int dy = rr % 3 - 1, dz = rr / 3 - 1;
                         const float ey = dy < 0 ? lyd : (dy > 0 ? uyd : 0.0f);
                         const float ez = dz < 0 ? lzd : (dz > 0 ? uzd : 0.0f);
                         const float dyz = ey * ey + ez * ez;
@@ -1263,85 +1226,59 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
                         if (q >= qe_full) continue;
                         int qe = qe_full;
                         if (qe - q > PAIR_HMAX - nh) {
-                            if (nh > 0) break;                   // evaluate first, resume here
+                            if (nh > 0) {                        // evaluate first, resume here
+                                stopped = true;
+                                break;
+                            }
                             qe = q + PAIR_HMAX;                  // a crowded row: part of it
                         }
-#ifndef DPD_V1
-#define DPD_V1 0
-#endif
-#if DPD_V1
-                        {   // queue [level][lane]: the staged slot of each hit.  Every
-                            // candidate is stored at the lane's next free level and the
-                            // level advances on a hit only; a row never holds more
-                            // candidates than free levels, so the stores stay in the queue
-                            int i = q - c0;
-                            const int ie = qe - c0;
-                            uint16_t *qp = my_q + nh * 32 + lane;
-                            for (; i + 1 < ie; i += 2) {   // two at a time
-                                const float4 pa = s_scan[i], pb = s_scan[i + 1];
-                                const float2 da = __fadd2_rn(make_float2(pa.x, pa.y), nxy);
-                                const float2 db = __fadd2_rn(make_float2(pb.x, pb.y), nxy);
-                                const float az = add_rn(pa.z, nzs), bz = add_rn(pb.z, nzs);
+                        {   // queue [level][lane]: the staged slot of each hit.  Shared
+                            // addresses are 32-bit window offsets; every candidate is
+                            // stored at the lane's next free level, which advances on a
+                            // hit only (a row never holds more candidates than free
+                            // levels, so the stores stay in the queue); the next pair
+                            // of candidates is loaded before this pair is tested
+                            uint32_t ad = scan_u32 + 16u * (uint32_t)(q - c0);
+                            const uint32_t ad_end = scan_u32 + 16u * (uint32_t)(qe - c0);
+                            uint32_t ent = (uint32_t)(q - c0);
+                            uint32_t qa = myq_u32 + 64u * (uint32_t)nh;
+                            float4 pa = lds128(ad), pb = lds128(ad + 16u);
+                            while (ad + 16u < ad_end) {   // two at a time
+                                const float4 ca = pa, cb = pb;
+                                ad += 32u;
+                                pa = lds128(ad);
+                                pb = lds128(ad + 16u);
+                                const float2 da = __fadd2_rn(make_float2(ca.x, ca.y), nxy);
+                                const float2 db = __fadd2_rn(make_float2(cb.x, cb.y), nxy);
+                                const float az = add_rn(ca.z, nzs), bz = add_rn(cb.z, nzs);
                                 const float ra = fma_rn(az, az, fma_rn(da.y, da.y, mul_rn(da.x, da.x)));
                                 const float rb = fma_rn(bz, bz, fma_rn(db.y, db.y, mul_rn(db.x, db.x)));
-                                const bool ha = ra < scan_lim && (P::kOffsets ? ra > 0.0f : i != (int)self);
-                                const bool hb = rb < scan_lim && (P::kOffsets ? rb > 0.0f : i + 1 != (int)self);
-                                *qp = (uint16_t)i;
-                                qp += ha ? 32 : 0;
-                                *qp = (uint16_t)(i + 1);
-                                qp += hb ? 32 : 0;
+                                const bool ha = ra < scan_lim && (P::kOffsets ? ra > 0.0f : ent != self);
+                                const bool hb = rb < scan_lim && (P::kOffsets ? rb > 0.0f : ent + 1u != self);
+                                sts16(qa, ent);
+                                qa += ha ? 64u : 0u;
+                                sts16(qa, ent + 1u);
+                                qa += hb ? 64u : 0u;
+                                ent += 2u;
                             }
-                            if (i < ie) {
-                                const float4 pj = s_scan[i];
-                                const float2 d = __fadd2_rn(make_float2(pj.x, pj.y), nxy);
-                                const float dzv = add_rn(pj.z, nzs);
+                            if (ad < ad_end) {   // an odd last candidate (already loaded)
+                                const float2 d = __fadd2_rn(make_float2(pa.x, pa.y), nxy);
+                                const float dzv = add_rn(pa.z, nzs);
                                 const float r2 = fma_rn(dzv, dzv, fma_rn(d.y, d.y, mul_rn(d.x, d.x)));
-                                const bool h = r2 < scan_lim && (P::kOffsets ? r2 > 0.0f : i != (int)self);
-                                *qp = (uint16_t)i;
-                                qp += h ? 32 : 0;
-                                ++i;
+                                const bool h = r2 < scan_lim && (P::kOffsets ? r2 > 0.0f : ent != self);
+                                sts16(qa, ent);
+                                qa += h ? 64u : 0u;
+                                ++ent;
                             }
-                            q = i + c0;
-                            nh = (int)((qp - my_q) >> 5);
+                            q = (int)ent + c0;
+                            nh = (int)((qa - myq_u32) >> 6);
                         }
-#else
-                        {   // queue [level][lane]: the staged slot of each hit
-                            const float4 *pp = s_scan + (q - c0);
-                            uint16_t ent = (uint16_t)(q - c0);
-                            uint16_t *qp = my_q + nh * 32 + lane;
-                            for (; q + 1 < qe; q += 2, pp += 2, ent += 2) {   // two at a time
-                                const float4 pa = pp[0], pb = pp[1];
-                                const float2 da = __fadd2_rn(make_float2(pa.x, pa.y), nxy);
-                                const float2 db = __fadd2_rn(make_float2(pb.x, pb.y), nxy);
-                                const float az = add_rn(pa.z, nzs), bz = add_rn(pb.z, nzs);
-                                const float ra = fma_rn(az, az, fma_rn(da.y, da.y, mul_rn(da.x, da.x)));
-                                const float rb = fma_rn(bz, bz, fma_rn(db.y, db.y, mul_rn(db.x, db.x)));
-                                if (ra < scan_lim && (P::kOffsets ? ra > 0.0f : ent != self)) {
-                                    *qp = ent;
-                                    qp += 32;
-                                }
-                                if (rb < scan_lim &&
-                                    (P::kOffsets ? rb > 0.0f : (uint16_t)(ent + 1) != self)) {
-                                    *qp = (uint16_t)(ent + 1);
-                                    qp += 32;
-                                }
-                            }
-                            if (q < qe) {
-                                const float4 pj = *pp;
-                                const float2 d = __fadd2_rn(make_float2(pj.x, pj.y), nxy);
-                                const float dzv = add_rn(pj.z, nzs);
-                                const float r2 = fma_rn(dzv, dzv, fma_rn(d.y, d.y, mul_rn(d.x, d.x)));
-                                if (r2 < scan_lim && (P::kOffsets ? r2 > 0.0f : ent != self)) {
-                                    *qp = ent;
-                                    qp += 32;
-                                }
-                                ++q;
-                            }
-                            nh = (int)((qp - my_q) >> 5);
+                        if (q < qe_full) {
+                            stopped = true;
+                            break;
                         }
-#endif
-                        if (q < qe_full) break;
                     }
+                    if (!stopped) r9 = 9;
                     more = r9 < 9;
                 }
             };
@@ -1418,6 +1355,17 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) 
         }
         __syncwarp();
     }
+    if (REUSE) {
+        __syncthreads();
+        if (tid == 0) mbar_inval(&s_mbar);
+    }
+    return true;
+}
+
+template <class P, int T, bool SAMPLE>
+__global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) k_pair(PairLaunch<P> la) {
+    griddep_wait();
+    pair_brick<P, T, SAMPLE>(la, la.br_lo + blockIdx.x);
 }
 
 // --------------------------------------------------------------------------
@@ -1463,12 +1411,18 @@ struct BondArgs {
     int b_lo, b_hi;
     const SysDesc<P> *sys;
     const int *bsys;
+    int sys1;                        // the only system of a batch of one, else -1
     const vec4 *fpair, *pos;
     const uint32_t *key;
     const int32_t *id, *inv_perm;
     const int32_t *bptr;   // [bead0 + id] -> first record (pool offset)
     const int32_t *bpartner;   // partner's local id
     const vec4 *bpar;      // r0, k, alpha, kind
+    // v and f of the step in the previous order, read through the source slot
+    // of each bead (the sort's gather does not move them; it records the
+    // source slots in `from`); written in the new order to vel, frc
+    const uint32_t *from;
+    const vec4 *vel_old, *frc_old;
     vec4 *vel, *frc, *ev;
     // the next step's update (FUSE): as UpdArgs
     vec4 *pos_tmp;
@@ -1504,20 +1458,21 @@ __device__ __forceinline__ void bond_disp(const BondArgs<P> &a, const SysDesc<P>
     }
 }
 
-template <class P, bool INIT, bool SAMPLE, bool FUSE = false>
-__global__ void __launch_bounds__(256) k_bond_vel(BondArgs<P> a) {
-    griddep_wait();
+template <class P, bool INIT, bool SAMPLE, bool FUSE>
+__device__ __forceinline__ void bond_vel_one(const BondArgs<P> &a, int t) {
     static_assert(!FUSE || !INIT, "the fused update follows a velocity update");
     using real = typename P::real;
     using vec4 = typename P::vec4;
-    const int t = a.b_lo + blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.b_hi) return;
-    const int sysi = a.bsys[t];
+    const int sysi = bead_sys(a, t);
     const SysDesc<P> &D = a.sys[sysi];
     const vec4 fp = a.fpair[t];
     real fx = fp.x, fy = fp.y, fz = fp.z, wb = 0, eb = 0;
-    const int32_t i = a.id[t];
-    const int b0 = a.bptr[D.bead0 + i], b1 = a.bptr[D.bead0 + i + 1];
+    int b0 = 0, b1 = 0;
+    if (a.bptr) {   // null when no resident system has bonds
+        const int32_t i = a.id[t];
+        b0 = a.bptr[D.bead0 + i];
+        b1 = a.bptr[D.bead0 + i + 1];
+    }
     for (int b = b0; b < b1; ++b) {
         const int u = a.inv_perm[D.bead0 + a.bpartner[b]];
         const vec4 bp = a.bpar[b];
@@ -1533,12 +1488,16 @@ __global__ void __launch_bounds__(256) k_bond_vel(BondArgs<P> a) {
         }
     }
     vec4 vn = mk4<vec4, real>((real)0, (real)0, (real)0, (real)0);
+    const uint32_t so = a.from[t];
     if (!INIT) {
         const real hdt = D.half_dt;
-        const vec4 v = a.vel[t], f = a.frc[t];
+        const vec4 v = a.vel_old[so], f = a.frc_old[so];
         vn = mk4<vec4, real>(v.x + hdt * (f.x + fx), v.y + hdt * (f.y + fy),
                              v.z + hdt * (f.z + fz), (real)0);
         a.vel[t] = vn;
+    } else {   // the initial force: v stays, moved into the new order
+        const vec4 v = a.vel_old[so];
+        a.vel[t] = mk4<vec4, real>(v.x, v.y, v.z, (real)0);
     }
     const vec4 fn = mk4<vec4, real>(fx, fy, fz, (real)0);
     a.frc[t] = fn;
@@ -1560,6 +1519,13 @@ __global__ void __launch_bounds__(256) k_bond_vel(BondArgs<P> a) {
     }
 }
 
+template <class P, bool INIT, bool SAMPLE, bool FUSE = false>
+__global__ void __launch_bounds__(256) k_bond_vel(BondArgs<P> a) {
+    griddep_wait();
+    const int t = a.b_lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < a.b_hi) bond_vel_one<P, INIT, SAMPLE, FUSE>(a, t);
+}
+
 // Bond virial and energy of every bead's bond records (ev.z, ev.w), from the
 // current positions and nothing else written: the bond half of an observables
 // pass made on demand, with the rounded accumulation of the sampled k_bond_vel.
@@ -1570,10 +1536,14 @@ __global__ void __launch_bounds__(256) k_bond_obs(BondArgs<P> a) {
     using vec4 = typename P::vec4;
     const int t = a.b_lo + blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= a.b_hi) return;
-    const SysDesc<P> &D = a.sys[a.bsys[t]];
+    const SysDesc<P> &D = a.sys[bead_sys(a, t)];
     real wb = 0, eb = 0;
-    const int32_t i = a.id[t];
-    const int b0 = a.bptr[D.bead0 + i], b1 = a.bptr[D.bead0 + i + 1];
+    int b0 = 0, b1 = 0;
+    if (a.bptr) {
+        const int32_t i = a.id[t];
+        b0 = a.bptr[D.bead0 + i];
+        b1 = a.bptr[D.bead0 + i + 1];
+    }
     for (int b = b0; b < b1; ++b) {
         const int u = a.inv_perm[D.bead0 + a.bpartner[b]];
         const vec4 bp = a.bpar[b];

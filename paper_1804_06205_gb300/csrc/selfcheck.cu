@@ -9,6 +9,13 @@
 // left in flight, so the context stays usable.  The source and the status word
 // are file-scope device variables: the call allocates nothing.
 //
+// dpd_grid_wait_check: the same for the grid-wide barrier of the persistent
+// step kernel.  A small cooperative grid meets at one barrier that expects
+// either exactly the grid (it completes) or one block more (nobody can
+// complete it: every block gives up after its clock budget and records
+// ST_TIMEOUT).  The barrier words and the status are file-scope device
+// variables, cleared before the launch.
+//
 // dpd_bm_check: the FP64 Box-Muller logarithm and cosine (ln_u24, cos_u24)
 // against the library's log and cospi over all 2^23 uniforms n 2^-24; returns
 // the largest absolute differences.
@@ -18,11 +25,14 @@
 
 #include "dpd.h"
 #include "kernels.cuh"
+#include "persist.cuh"
 
 namespace {
 
 static __device__ __align__(16) unsigned char g_wc_src[16];
 static __device__ int g_wc_status;
+static __device__ dpd::GridBar g_gw_bar;
+static __device__ int g_gw_status;
 
 __global__ void k_wait_check(int deliver, int tries) {
     __shared__ __align__(16) unsigned char buf[16];
@@ -104,4 +114,42 @@ extern "C" int dpd_wait_check(int32_t deliver, int32_t tries, void *cuda_stream)
         return DPD_ECUDA;
     if (status & dpd::ST_TIMEOUT) return DPD_ETIMEOUT;
     return status ? DPD_ECUDA : DPD_OK;
+}
+
+extern "C" int dpd_grid_wait_check(int32_t complete, int64_t budget_cycles, void *cuda_stream) {
+    if (budget_cycles <= 0 || budget_cycles > DPD_GRID_WAIT_CHECK_MAX_CYCLES) return DPD_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const dpd::GridBar zb = {0u, 0u};
+    const int zero = 0;
+    if (cudaMemcpyToSymbolAsync(g_gw_bar, &zb, sizeof(zb), 0, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyToSymbolAsync(g_gw_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess)
+        return DPD_ECUDA;
+    dpd::GridBar *bar = nullptr;
+    int *status = nullptr;
+    if (cudaGetSymbolAddress((void **)&bar, g_gw_bar) != cudaSuccess ||
+        cudaGetSymbolAddress((void **)&status, g_gw_status) != cudaSuccess)
+        return DPD_ECUDA;
+    constexpr unsigned int kGrid = 4;   // co-resident on any GPU
+    const unsigned int expect = complete ? kGrid : kGrid + 1;
+    const long long budget = (long long)budget_cycles;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kGrid);
+    cfg.blockDim = dim3(64);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, dpd::k_grid_wait_check, bar, expect, budget, status) != cudaSuccess)
+        return DPD_ECUDA;
+    int out = 0;
+    if (cudaMemcpyFromSymbolAsync(&out, g_gw_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return DPD_ECUDA;
+    if (out & dpd::ST_TIMEOUT) return DPD_ETIMEOUT;
+    return out ? DPD_ECUDA : DPD_OK;
 }

@@ -38,7 +38,7 @@ EXPORTED = ("dpd_default_options", "dpd_create", "dpd_set_state", "dpd_step", "d
             "dpd_batch_last_error", "dpd_batch_destroy", "dpd_batch_profile_begin",
             "dpd_batch_profile_end", "dpd_wait_check", "dpd_bm_check", "dpd_checkpoint_bytes",
             "dpd_get_checkpoint", "dpd_set_checkpoint", "dpd_batch_checkpoint_bytes",
-            "dpd_batch_get_checkpoint", "dpd_batch_set_checkpoint")
+            "dpd_batch_get_checkpoint", "dpd_batch_set_checkpoint", "dpd_grid_wait_check")
 
 
 class dpd_box(C.Structure):
@@ -53,7 +53,8 @@ class dpd_bond(C.Structure):
 class dpd_options(C.Structure):
     _fields_ = [("lambda_", C.c_double), ("seed", C.c_uint64), ("precision", C.c_int32),
                 ("noise", C.c_int32), ("sample_every", C.c_int32), ("tile_cells", C.c_int32),
-                ("threads", C.c_int32), ("use_graph", C.c_int32), ("cuda_stream", C.c_void_p)]
+                ("threads", C.c_int32), ("use_graph", C.c_int32), ("persistent", C.c_int32),
+                ("pad", C.c_int32), ("cuda_stream", C.c_void_p)]
 
 
 class dpd_batch_capacity(C.Structure):
@@ -110,6 +111,8 @@ def _load():
     lib.dpd_cells_noalloc.argtypes = [P, C.c_int64, P, P, P, P, P]
     lib.dpd_wait_check.argtypes = [C.c_int32, C.c_int32, P]
     lib.dpd_wait_check.restype = C.c_int
+    lib.dpd_grid_wait_check.argtypes = [C.c_int32, C.c_int64, P]
+    lib.dpd_grid_wait_check.restype = C.c_int
     lib.dpd_bm_check.argtypes = [P, P]
     lib.dpd_bm_check.restype = C.c_int
     lib.dpd_checkpoint_bytes.argtypes = [P, P]
@@ -172,6 +175,18 @@ def wait_check(deliver, tries=4096, stream_ptr=None):
     (deliver=True, DPD_OK) or never delivered (deliver=False: the wait gives up
     after `tries` polls, DPD_ETIMEOUT).  Returns the DPD_* code."""
     return lib.dpd_wait_check(1 if deliver else 0, int(tries), C.c_void_p(stream_ptr))
+
+
+GRID_WAIT_CHECK_MAX_CYCLES = 4000000000
+
+
+def grid_wait_check(complete, budget_cycles=20_000_000, stream_ptr=None):
+    """dpd_grid_wait_check: one grid-wide barrier of a 4-block cooperative
+    grid that completes (complete=True, DPD_OK) or waits for a block that does
+    not exist (complete=False: every block gives up after budget_cycles,
+    DPD_ETIMEOUT).  Returns the DPD_* code."""
+    return lib.dpd_grid_wait_check(1 if complete else 0, int(budget_cycles),
+                                   C.c_void_p(stream_ptr))
 
 
 def bm_check():

@@ -91,3 +91,10 @@ def test_create_rejects_boxes_with_too_many_cells(binding, L):
         binding.System(L, np.zeros(4, np.int32), np.array([[25.0]]), 4.5, 1.0, 0.04)
     assert e.value.code == binding.DPD_EINVAL
     assert "too many cells" in str(e.value)
+
+
+def test_grid_wait_check_rejects_bad_arguments(binding):
+    # argument checks come before any CUDA call
+    assert binding.grid_wait_check(True, budget_cycles=0) == binding.DPD_EINVAL
+    assert binding.grid_wait_check(
+        True, budget_cycles=binding.GRID_WAIT_CHECK_MAX_CYCLES + 1) == binding.DPD_EINVAL
