@@ -8,22 +8,31 @@ the whole system, on the device.
 Default workload: the 100^3 periodic box at rho = 3 (N = 3,000,000), types
 A/B 50/50, a_AA = a_BB = 25, a_AB = 30, gamma = 4.5, kT = 1, dt = 0.04;
 synthetic, seeded.  Prints ONE JSON line (rank 0):
-  value   FP32 particle-steps/s, state resident in HBM (CUDA-graph replay)
+  value   FP32 particle-steps/s, state resident in HBM, the step kernels
+          launched directly (programmatic dependent launch) on one stream
   e2e     the same metric through the public API with host buffers: every
           step sets the state from pinned host memory, steps, reads it back
-  fp64_plain  the plain FP64 path, one system per launch
-  roofline    the pair kernel (dominant) against the ALU issue peak
-  cpu_baseline  the FP64 oracle (cell-list mode) on the host cores
+  roofline    the pair kernel (dominant) against the plain-ALU issue peak,
+          with the algorithmic operation count of the method per bead
+  roofline_hbm_phases  cell division and bonds/velocity/update against the
+          HBM peak, with the method's minimum bytes per bead
+  cpu_baseline  the FP64 oracle (cell-list mode) on the host cores; the same
+          leg measures each path's one-evaluation force error against the
+          oracle's brute-force sum on sampled beads (error_vs_oracle)
   paper_tables  the shapes of the paper's Tables 1 and 3 (N = 5k..100k) on
           the GPU, beside CAMUS's quoted CPU times (context)
   alpha_helix   the paper's alpha-helix run, 10,000 steps
   serving the batched half of the metric: a stream of independent systems
           (box edge 8..24, two types, 10% of beads in chains) arriving as a
           Poisson process, served by continuous batching; p50/p99 completion
-          latency and throughput, after the autotuner picked the launch shape
+          latency and throughput, after the autotuner picked the launch shape;
+          serving_saturated: the same stream all arriving at once
+  fp64_plain    the plain FP64 path, one system per launch (last in the line)
 
 --impl reference times the FP64 CPU oracle (the only reference: the paper
 publishes no code) on a bounded sample of the same workload.
+--profile-target WORKLOAD runs set_state and a few steps of a named
+workload (a target for kernel profilers; prints nothing else).
 Multi-GPU: replicas only (each rank advances its own copy; value sums them).
 """
 from __future__ import annotations
@@ -46,32 +55,40 @@ UNIT = "particle-steps/s"
 WORKLOAD_DESC = ("fluid_3m: periodic 100^3 box, rho=3, N=3,000,000, types A/B 50/50, "
                  "a_AA=a_BB=25, a_AB=30, gamma=4.5 (sigma=3), kT=1, dt=0.04, lambda=0.65")
 
-# Algorithmic work of one pair-force evaluation (per bead, per step, rho = 3),
-# counted from the method: each unique candidate pair in the 27-cell half
-# shell (40.5 per bead) costs a distance test of 7 ops (3 sub, 3 mul/fma,
-# 1 compare); each unique pair within r_c (6.28 per bead) costs 103 ops
-# (r, w, e, v_ij.e: 13; Philox4x32-10: 60; two uniforms: 6; Box-Muller: 6;
-# scalar force: 8; vector force: 3; add to both beads: 6; id order: 2).
-PAIR_OPS_PER_BEAD = 40.5 * 7 + 6.28 * 103
-# Minimum HBM bytes of the other phases (per bead per step, FP32 path).
-# Sort (scans, scatter, gather): the scans ~4 B; the scatter reads system,
-# key, rank and id (16 B) plus the cell start and writes source and id (8 B);
-# the gather reads source, id, key and cell bounds (~16 B) and the moving
-# state pos/vel/frc (48 B), then writes pos/key/vel/frc/id/v~ (72 B): 172 B.
-# Bonds + velocity, which also make the next step's position update: read
-# f_pair/vel/frc/pos/key/id/system (68 B), write vel/frc/pos'/key'/rank and
-# the cell count (60 B), plus the bond table pointers: ~144 B.
-SORT_BYTES_PER_BEAD = 172.0
-# DRAM bytes (read + written) per bead of one k_pair launch, from an ncu
-# capture of the current pair kernel on this workload (dram__bytes_read.sum +
-# dram__bytes_write.sum = 144.8 MB for 3,000,000 beads; the algorithmic
-# minimum is 48 B per bead).
-PAIR_DRAM_BYTES_PER_BEAD = 48.27
-# Thread instructions executed per bead by one k_pair launch, from the same
-# capture (smsp__inst_executed.sum x thread_inst_executed_per_inst_executed):
-# the issued work, against which the issue-rate roofline is taken.
-PAIR_THREAD_INST_PER_BEAD = 4384.0
-BOND_BYTES_PER_BEAD = 144.0
+# Algorithmic work of one step of the pair force, per bead at rho = 3, as
+# the method requires it (each unique pair counted once): 40.5 candidate
+# pairs in the half shell of 27 cells at ~8 FP32 ops (3 sub, 3 mul/fma,
+# compare), and 6.28 unique pairs within r_c at ~150 ops (distance, weight,
+# projections and force ~35 FP32; Philox4x32-10 ~100 INT32; Box-Muller ~3
+# transcendentals + ~8 FP32).
+PAIR_OPS_PER_BEAD = 40.5 * 8 + 6.28 * 150
+# The same work recounted from the kernel's own operations (7 ops per
+# candidate test; 103 per unique pair: geometry 13, Philox 60, uniforms 6,
+# Box-Muller 6, force 11, sums 6, id order 2), reported beside it.
+PAIR_OPS_PER_BEAD_RECOUNT = 40.5 * 7 + 6.28 * 103
+# Minimum HBM bytes per bead and step of the two HBM-bound phases together
+# (cell division, bonds + velocity + position update): the state (offset
+# 16 B, velocity 16 B, force 16 B, id and key 8 B) read once and written
+# once, doubled by the sort's gather: 200 B.
+HBM_MIN_BYTES_PER_BEAD = 200.0
+PROFILE_FIGURES = os.path.join(ROOT, "profiles", "k_pair_fluid_3m.md")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_1804_06205_gb300", "csrc", "kernels.cuh")
+
+
+def profile_figures():
+    """ncu figures of one k_pair launch on fluid_3m, from the committed
+    profile, if they were taken on the current kernel source (else None)."""
+    import hashlib
+    import re
+    try:
+        text = open(PROFILE_FIGURES).read()
+        m = re.search(r"<!-- figures (\{.*?\}) -->", text)
+        fig = json.loads(m.group(1))
+        sha = hashlib.sha1(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+    except Exception:
+        return None
+    fig["current"] = fig.get("kernel_source_sha1") == sha
+    return fig
 
 
 def _peaks():
@@ -181,6 +198,25 @@ def run_cpu_oracle(w, warmup, steps):
     return w.n * steps / dt, dt, O.num_threads()
 
 
+def oracle_force_error(w, forces, step, nsample=256, seed=12):
+    """One force evaluation of each GPU path against the FP64 oracle's
+    brute-force pair sum on `nsample` beads drawn with a fixed seed:
+    max |f_gpu - f_oracle| / max |f_oracle| over the sample (per path)."""
+    import oracle as O
+    s = O.System(w.L, w.types, w.a, w.gamma, w.kT, w.dt, w.lam, seed=w.seed, bonds=w.bonds)
+    idx = np.random.default_rng(seed).choice(w.n, nsample, replace=False)
+    t0 = time.perf_counter()
+    fo = O.pair_forces_subset(s, w.pos, w.vel, step, idx)
+    out = {"sampled_beads": nsample, "oracle_s": time.perf_counter() - t0,
+           "what": "one force evaluation from an identical state: max|f - f_oracle| / "
+                   "max|f_oracle| over the sampled beads (FP64 brute-force pair sum)"}
+    scale = float(np.abs(fo).max())
+    for name, f in forces.items():
+        out[name] = float(np.abs(f[idx] - fo).max()) / scale
+    out["tolerance"] = {"f32": 1e-4, "f64": 1e-10}
+    return out
+
+
 def reference_arm(args):
     from paper_1804_06205_gb300 import workloads as W
     ws, rank, _ = _dist()
@@ -263,16 +299,22 @@ def alpha_helix_leg(D, W, stream):
             "kT": o["kT"], "p_total": o["p_total"]}
 
 
-def serving_leg(args, stream):
-    """Continuous batching of a Poisson stream of independent systems."""
+def serving_leg(args, stream, saturated=False, table=None):
+    """Continuous batching of a stream of independent systems: Poisson
+    arrivals at the workload's rate, or (saturated) all of them at t = 0."""
     from paper_1804_06205_gb300 import autotune, serving
     from paper_1804_06205_gb300 import workloads as W
-    t0 = time.perf_counter()
-    table = autotune.tune(edges=(8.0, 12.0, 16.0, 20.0, 24.0), threads=(128, 256),
-                          beads=300_000, steps=8)
-    tune_s = time.perf_counter() - t0
+    tune_s = 0.0
+    if table is None:
+        t0 = time.perf_counter()
+        table = autotune.tune(edges=(8.0, 12.0, 16.0, 20.0, 24.0), threads=(128, 256),
+                              beads=300_000, steps=8)
+        tune_s = time.perf_counter() - t0
     reqs = W.serving_stream(nsys=args.serve_requests, rate_hz=args.serve_rate,
                             steps=args.serve_steps)
+    if saturated:
+        for r in reqs:
+            r.arrival_s = 0.0
     srv = serving.Server(max_beads=3_000_000, max_cells=1_500_000, max_bonds=600_000,
                          max_systems=160, chunk=args.serve_chunk, table=table,
                          cuda_stream=stream.cuda_stream)
@@ -284,16 +326,34 @@ def serving_leg(args, stream):
     launches = srv.batch.launch_count() - l0
     srv.close()
     out = serving.summarize(done)
-    out.update({"rate_hz": args.serve_rate, "steps_per_request": args.serve_steps,
-                "chunk_steps": args.serve_chunk, "max_resident": srv.max_resident,
-                "chunks": srv.chunks, "gpu_launches": launches, "clocks": clocks,
-                "autotune": table, "autotune_s": tune_s,
-                "workload": "serving stream: %d systems, box edge U(8,24), rho=3, types A/B, "
-                            "a_AB U(25,50), 10%% of beads in harmonic 10-mers, dt=0.04; "
-                            "Poisson arrivals at %g/s; FP32" % (args.serve_requests,
-                                                                args.serve_rate),
+    out.update({"arrivals": "all at t=0" if saturated else "Poisson %g/s" % args.serve_rate,
+                "steps_per_request": args.serve_steps, "chunk_steps": args.serve_chunk,
+                "max_resident": srv.max_resident, "chunks": srv.chunks,
+                "gpu_busy_frac": srv.busy_s / max(out["span_s"], 1e-9),
+                "gpu_launches": launches, "clocks": clocks,
                 "latency": "completion (final state on the host) - arrival"})
-    return out
+    if not saturated:
+        out.update({"autotune": table, "autotune_s": tune_s,
+                    "workload": "serving stream: %d systems, box edge U(8,24), rho=3, types A/B, "
+                                "a_AB U(25,50), 10%% of beads in harmonic 10-mers, dt=0.04; "
+                                "FP32" % args.serve_requests})
+    return out, table
+
+
+def profile_target(args):
+    """set_state and a few steps of a named workload, for kernel profilers."""
+    from paper_1804_06205_gb300 import build as B
+    B.build()
+    from paper_1804_06205_gb300 import dpd as D
+    from paper_1804_06205_gb300 import workloads as W
+    w = W.make(args.profile_target)
+    g = D.System.from_workload(w, precision=args.profile_precision,
+                               threads=args.profile_threads)
+    g.set_state(w.pos, w.vel, 0)
+    g.step(args.steps)
+    g.sync()
+    g.close()
+    return 0
 
 
 def main():
@@ -315,7 +375,12 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-steps", type=int, default=2000)
     ap.add_argument("--serve-chunk", type=int, default=50)
+    ap.add_argument("--profile-target", default=None, metavar="WORKLOAD")
+    ap.add_argument("--profile-precision", type=int, default=0)
+    ap.add_argument("--profile-threads", type=int, default=0)
     args = ap.parse_args()
+    if args.profile_target:
+        return profile_target(args)
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return reference_arm(args)
@@ -345,14 +410,16 @@ def main():
     from paper_1804_06205_gb300 import workloads as W
 
     w = W.make(args.workload)
-    # a dedicated stream: the legacy default stream cannot be graph-captured
+    # a dedicated stream for all of the library's work
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     peaks = _peaks()
+    err_step = 11          # evaluation counter of the error-check state
 
     def timed(prec, warmup, steps, profile=True, sampler=None):
         g = D.System.from_workload(w, precision=prec, cuda_stream=stream.cuda_stream)
-        g.set_state(w.pos, w.vel, 0)
+        g.set_state(w.pos, w.vel, err_step)
+        f0 = g.get_state(pos=False, vel=False)[2]     # for the oracle error, untimed
         g.step(warmup)
         barrier()
         if sampler:
@@ -375,20 +442,20 @@ def main():
             phases = (pms / max(pn, 1)).tolist()
         pairs = int(g.gr_counts(1.0, 1)[0])
         g.close()
-        return ms, launches, clocks, phases, pairs
+        return ms, launches, clocks, phases, pairs, f0
 
     # ---- FP32, state resident in HBM
     sampler = ClockSampler(local)
-    ms32, launches, clocks, phases, pairs = timed(D.DPD_FP32, args.warmup, args.steps,
-                                                  sampler=sampler)
+    ms32, launches, clocks, phases, pairs, f32 = timed(D.DPD_FP32, args.warmup, args.steps,
+                                                       sampler=sampler)
     value, secs32 = replica_throughput(w.n * args.steps, ms32 * 1e-3, dist, "cuda")
     ms32 = secs32 * 1e3
 
     # ---- plain FP64 path
-    fp64 = None
+    fp64, f64 = None, None
     if not args.no_fp64:
         k64 = args.fp64_steps or args.steps
-        ms64, _, _, ph64, _ = timed(D.DPD_FP64, max(3, args.warmup // 4), k64)
+        ms64, _, _, ph64, _, f64 = timed(D.DPD_FP64, max(3, args.warmup // 4), k64)
         ms64 = max_over_ranks(ms64)
         v64 = ws * w.n * k64 / (ms64 * 1e-3)
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / k64, "steps": k64,
@@ -416,48 +483,67 @@ def main():
     e2e = {"value": ws * w.n * args.e2e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": 2 * w.n * 3 * 8, "d2h_bytes_per_step": 2 * w.n * 3 * 8,
            "steps": args.e2e_steps,
-           "note": "per step: dpd_set_state from pinned host (pos, vel) incl. its force "
-                   "evaluation, dpd_step(1), dpd_get_state to pinned host (pos, vel)"}
+           "note": "per step: dpd_set_state from pinned host (pos, vel), which evaluates f "
+                   "at the new state, dpd_step(1), dpd_get_state to pinned host (pos, vel)"}
 
     # ---- roofline of the pair kernel (plain-ALU bound)
     pair_ms = phases[1]
     alu_peak = 152 * 128 * peaks["sm_max_mhz"] * 1e6          # lane-ops/s at max SM clock
     achieved = PAIR_OPS_PER_BEAD * w.n / (pair_ms * 1e-3)
+    fig = profile_figures()
+    cur = bool(fig and fig.get("current"))
+    scale = w.n / fig["n"] if cur else None
     roofline = {"bound": "alu", "kernel": "k_pair", "achieved": achieved / 1e12,
                 "peak": alu_peak / 1e12, "unit": "Tops/s", "frac": achieved / alu_peak,
-                "traffic": PAIR_DRAM_BYTES_PER_BEAD * w.n,
-                "traffic_note": "bytes per launch: ncu dram read+write of one launch on this workload",
-                "ops_per_bead": PAIR_OPS_PER_BEAD, "launch_ms": pair_ms,
-                "issued": {"thread_inst_per_bead": PAIR_THREAD_INST_PER_BEAD,
-                           "achieved": PAIR_THREAD_INST_PER_BEAD * w.n / (pair_ms * 1e-3) / 1e12,
-                           "frac": PAIR_THREAD_INST_PER_BEAD * w.n / (pair_ms * 1e-3) / alu_peak,
-                           "unit": "T thread-instructions/s",
-                           "note": "instructions the kernel issues (ncu), against the same peak"},
+                "traffic": fig["dram_bytes"] * scale if cur else None,
+                "traffic_note": ("ncu dram read+write of one launch (profiles/k_pair_fluid_3m.md, "
+                                 "taken on this kernel source)" if cur else
+                                 "null: the committed ncu figures predate the current kernel"),
+                "ops_per_bead": PAIR_OPS_PER_BEAD,
+                "ops_per_bead_recount": PAIR_OPS_PER_BEAD_RECOUNT,
+                "frac_recount": PAIR_OPS_PER_BEAD_RECOUNT * w.n / (pair_ms * 1e-3) / alu_peak,
+                "launch_ms": pair_ms,
                 "peak_source": "152 SMs x 128 lanes x %.0f MHz (one op per lane per cycle)"
                                % peaks["sm_max_mhz"]}
+    if cur:
+        ti = fig["thread_inst"] * scale
+        roofline["issued"] = {"thread_inst_per_bead": ti / w.n,
+                              "frac": ti / (pair_ms * 1e-3) / alu_peak,
+                              "note": "thread instructions the kernel issues (ncu), same peak"}
+    hbm_ms = phases[0] + phases[2]
+    hbm = {"bytes_per_bead": HBM_MIN_BYTES_PER_BEAD, "ms": hbm_ms,
+           "GBs": HBM_MIN_BYTES_PER_BEAD * w.n / (hbm_ms * 1e-3) / 1e9,
+           "frac": HBM_MIN_BYTES_PER_BEAD * w.n / (hbm_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+           "phases_ms": {"update_sort": phases[0], "bond_vel": phases[2]},
+           "peak_GBs": peaks["hbm_gbs"], "peak_source": peaks["source"],
+           "note": "cell division + bonds/velocity/update against the method's minimum "
+                   "bytes (state read and written once, doubled by the sort's gather)"}
     step_ms = ms32 / args.steps
-    other = {
-        "update_sort": {"ms": phases[0], "bytes_per_bead": SORT_BYTES_PER_BEAD,
-                        "GBs": SORT_BYTES_PER_BEAD * w.n / (phases[0] * 1e-3) / 1e9},
-        "bond_vel": {"ms": phases[2], "bytes_per_bead": BOND_BYTES_PER_BEAD,
-                     "GBs": BOND_BYTES_PER_BEAD * w.n / (phases[2] * 1e-3) / 1e9},
-        "hbm_peak_GBs": peaks["hbm_gbs"], "peak_source": peaks["source"]}
 
-    cpu = None
+    # ---- the oracle on the host: timing, and each path's force error
+    cpu = err = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, secs, cores = run_cpu_oracle(w, 1, args.cpu_steps)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "FP64 oracle, cell-list mode, full fluid_3m (N=3,000,000), 1 warm-up + "
                          "%d timed steps on all host cores" % args.cpu_steps}
+        forces = {"f32": f32}
+        if f64 is not None:
+            forces["f64"] = f64
+        err = oracle_force_error(w, forces, err_step)
 
-    serve = tables = helix = None
+    serve = serve_sat = tables = helix = None
     if ws == 1 and not args.no_serving:
-        serve = serving_leg(args, stream)
+        serve, table = serving_leg(args, stream)
+        serve_sat, _ = serving_leg(args, stream, saturated=True, table=table)
     if ws == 1 and not args.no_extras:
         tables = paper_tables_leg(D, W, stream)
         helix = alpha_helix_leg(D, W, stream)
 
     if rank == 0:
+        keep = lambda d, ks: None if d is None else {k: d[k] for k in ks if k in d}
+        skeys = ("requests", "arrivals", "p50_latency_s", "p99_latency_s",
+                 "throughput_particle_steps_per_s", "max_resident", "gpu_busy_frac")
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -465,11 +551,16 @@ def main():
                 "config": {"workload": WORKLOAD_DESC, "N": w.n,
                            "l2": "inputs larger than L2 (~0.5 GB of state per replica)",
                            "parallelism": "replicas" if ws > 1 else "single"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clocks,
+                # bulky context first; the tail of the line keeps the key results
+                "paper_tables": tables, "alpha_helix": helix,
+                "serving_detail": serve, "serving_saturated_detail": serve_sat,
                 "pair_interactions_per_s": ws * pairs * args.steps / (ms32 * 1e-3),
                 "phases_ms": dict(zip(("update_sort", "pair", "bond_vel"), phases)),
-                "fp64_plain": fp64, "roofline": roofline, "roofline_hbm_phases": other,
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-                "serving": serve, "paper_tables": tables, "alpha_helix": helix}
+                "roofline_hbm_phases": hbm,
+                "serving": keep(serve, skeys), "serving_saturated": keep(serve_sat, skeys),
+                "error_vs_oracle": err, "fp64_plain": fp64}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -74,6 +74,7 @@ class Server:
         self.clock = clock
         self.max_resident = 0
         self.chunks = 0
+        self.busy_s = 0.0     # host time spent waiting for chunks (the GPU is busy)
 
     def run(self, requests: Sequence[Request]) -> List[Completed]:
         """Serve the requests in real time (arrival_s relative to the start)."""
@@ -102,8 +103,10 @@ class Server:
                     time.sleep(max(0.0, pending[0].arrival_s - (self.clock() - t0)))
                 continue
             k = min(self.chunk, min(v[1] for v in resident.values()))
+            tb = self.clock()
             b.step(k)
             b.sync()
+            self.busy_s += self.clock() - tb
             self.chunks += 1
             for v in resident.values():
                 v[1] -= k

@@ -54,7 +54,7 @@ def fake_server(cap, chunk):
     srv = serving.Server.__new__(serving.Server)
     srv.batch = FakeBatch(cap)
     srv.chunk, srv.table, srv.keep = chunk, None, True
-    srv.clock, srv.max_resident, srv.chunks = FakeClock(), 0, 0
+    srv.clock, srv.max_resident, srv.chunks, srv.busy_s = FakeClock(), 0, 0, 0.0
     return srv
 
 
