@@ -9,6 +9,8 @@ file only marshals numpy arrays.
 What each function computes, with the passage it follows:
   * ``pair_forces``  eq. 3-4 plus the Groot-Warren dissipative/random forms
     (w^D = (w^R)^2, sigma^2 = 2 gamma kT), brute force over all j != i;
+    ``pair_forces_ids`` the same terms for beads given with their global ids
+    (a spatial domain and its ghosts, ``oracle.slab``);
   * ``bond_forces``  eqs. 6-8, Fig. 3a;
   * ``run``          Fig. 1 (modified velocity-Verlet, lambda);
   * ``cell_keys`` / ``cell_sort``  the cell division of section "Design
@@ -84,6 +86,8 @@ def _load():
             lib.orc_pair_force_one.argtypes = [P, P, P, C.c_int64, C.c_int64, C.c_int64, P]
             lib.orc_pair_forces.argtypes = [P, P, P, C.c_int64, C.c_int32, P, P]
             lib.orc_pair_forces_subset.argtypes = [P, P, P, C.c_int64, P, C.c_int64, P]
+            lib.orc_pair_forces_ids.argtypes = [P, C.c_int64, P, P, P, P, C.c_int64, C.c_int64,
+                                                P]
             lib.orc_bond_forces.argtypes = [P, P, P, P]
             lib.orc_bond_one.argtypes = [C.c_int32, C.c_double, C.c_double, C.c_double, P, P, P]
             lib.orc_forces.argtypes = [P, P, P, C.c_int64, C.c_int32, P, P]
@@ -193,6 +197,23 @@ def pair_forces_subset(sys: System, pos, vt, s, idx):
                                         int(idx.size), _ptr(f))
     if rc:
         raise RuntimeError("orc_pair_forces_subset failed: %d" % rc)
+    return f
+
+
+def pair_forces_ids(sys: System, pos, vt, types, ids, m, s):
+    """Pair forces on the first m of the given beads (their own positions,
+    predicted velocities, types and global ids) from all of them: a domain's
+    beads followed by its ghosts."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    vt = np.ascontiguousarray(vt, dtype=np.float64).reshape(-1, 3)
+    types = np.ascontiguousarray(types, dtype=np.int32)
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    n = pos.shape[0]
+    f = np.zeros((int(m), 3))
+    rc = _load().orc_pair_forces_ids(sys.ref, n, _ptr(pos), _ptr(vt), _ptr(types), _ptr(ids),
+                                     int(m), int(s), _ptr(f))
+    if rc:
+        raise RuntimeError("orc_pair_forces_ids failed: %d" % rc)
     return f
 
 

@@ -73,22 +73,23 @@ double orc_theta(uint64_t seed, int64_t i, int64_t j, int64_t s, int32_t noise) 
 /* ------------------------------------------------------------------------ */
 static inline double min_image(double d, double L) { return d - L * nearbyint(d / L); }
 
-/* Returns 1 and fills F, the conservative virial d.F^C and the pair energy if
- * 0 < r < 1, else returns 0. */
-static int pair_core(const orc_sys *sys, const double *pos, const double *vt, int64_t i,
-                     int64_t j, int64_t s, double F[3], double *wc, double *ep) {
+/* The pair terms for bead i (position pi, predicted velocity vi, type ti,
+ * id idi) and bead j: returns 1 and fills F (force on i), the conservative
+ * virial d.F^C and the pair energy if 0 < r < 1, else returns 0. */
+static int pair_terms(const orc_sys *sys, const double *pi, const double *pj, const double *vi,
+                      const double *vj, int32_t ti, int32_t tj, int64_t idi, int64_t idj,
+                      int64_t s, double F[3], double *wc, double *ep) {
     double d[3];
-    for (int k = 0; k < 3; ++k) d[k] = min_image(pos[3 * i + k] - pos[3 * j + k], sys->L[k]);
+    for (int k = 0; k < 3; ++k) d[k] = min_image(pi[k] - pj[k], sys->L[k]);
     double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     if (r2 >= 1.0 || r2 == 0.0) return 0;
     double r = sqrt(r2);
     double e[3] = {d[0] / r, d[1] / r, d[2] / r};
     double w = 1.0 - r;                                      /* w^R(r) */
-    double a = sys->a[sys->types[i] * sys->ntypes + sys->types[j]];
-    double ev = e[0] * (vt[3 * i] - vt[3 * j]) + e[1] * (vt[3 * i + 1] - vt[3 * j + 1]) +
-                e[2] * (vt[3 * i + 2] - vt[3 * j + 2]);
+    double a = sys->a[ti * sys->ntypes + tj];
+    double ev = e[0] * (vi[0] - vj[0]) + e[1] * (vi[1] - vj[1]) + e[2] * (vi[2] - vj[2]);
     double sigma = sqrt(2.0 * sys->gamma * sys->kT);
-    double theta = orc_theta(sys->seed, i, j, s, sys->noise);
+    double theta = orc_theta(sys->seed, idi, idj, s, sys->noise);
     double fc = a * w;                                       /* eq. 4 */
     double fd = -sys->gamma * w * w * ev;                    /* w^D = (w^R)^2 */
     double fr = sigma * w * theta / sqrt(sys->dt);           /* random term */
@@ -99,6 +100,13 @@ static int pair_core(const orc_sys *sys, const double *pos, const double *vt, in
     *wc = r * fc;
     *ep = 0.5 * a * w * w;
     return 1;
+}
+
+/* Bead index = bead id: the system's own arrays. */
+static int pair_core(const orc_sys *sys, const double *pos, const double *vt, int64_t i,
+                     int64_t j, int64_t s, double F[3], double *wc, double *ep) {
+    return pair_terms(sys, pos + 3 * i, pos + 3 * j, vt + 3 * i, vt + 3 * j, sys->types[i],
+                      sys->types[j], i, j, s, F, wc, ep);
 }
 
 void orc_pair_force_one(const orc_sys *sys, const double *pos, const double *vt, int64_t i,
@@ -259,6 +267,33 @@ int orc_pair_forces_subset(const orc_sys *sys, const double *pos, const double *
             if (j == i) continue;
             double F[3], wc, ep;
             if (pair_core(sys, pos, vt, i, j, s, F, &wc, &ep)) {
+                fi[0] += F[0]; fi[1] += F[1]; fi[2] += F[2];
+            }
+        }
+        f[3 * q] = fi[0]; f[3 * q + 1] = fi[1]; f[3 * q + 2] = fi[2];
+    }
+    return 0;
+}
+
+/* Pair forces on the first m of n beads given by their own arrays (positions,
+ * predicted velocities, types and global ids), summed over all n beads j != q
+ * in the order given: the same terms as orc_pair_forces for any subset of a
+ * system that holds every bead within r_c of the targets (a domain and its
+ * ghosts). */
+int orc_pair_forces_ids(const orc_sys *sys, int64_t n, const double *pos, const double *vt,
+                        const int32_t *types, const int64_t *ids, int64_t m, int64_t s,
+                        double *f) {
+    if (m < 0 || m > n) return -3;
+    for (int64_t q = 0; q < n; ++q)
+        if (types[q] < 0 || types[q] >= sys->ntypes) return -3;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t q = 0; q < m; ++q) {
+        double fi[3] = {0, 0, 0};
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == q) continue;
+            double F[3], wc, ep;
+            if (pair_terms(sys, pos + 3 * q, pos + 3 * j, vt + 3 * q, vt + 3 * j, types[q],
+                           types[j], ids[q], ids[j], s, F, &wc, &ep)) {
                 fi[0] += F[0]; fi[1] += F[1]; fi[2] += F[2];
             }
         }

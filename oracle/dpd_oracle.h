@@ -82,6 +82,9 @@ int orc_pair_forces(const orc_sys *sys, const double *pos, const double *vt,
 int orc_pair_forces_subset(const orc_sys *sys, const double *pos, const double *vt, int64_t s,
                            const int64_t *idx, int64_t m, double *f);
 /* Bond forces added into f[n*3]. */
+int orc_pair_forces_ids(const orc_sys *sys, int64_t n, const double *pos, const double *vt,
+                        const int32_t *types, const int64_t *ids, int64_t m, int64_t s,
+                        double *f);
 int orc_bond_forces(const orc_sys *sys, const double *pos, double *f, orc_terms *t);
 /* Force and energy of one bond record on bead i (F_j = -F_i). */
 void orc_bond_one(int32_t kind, double r0, double k, double alpha, const double d[3],
