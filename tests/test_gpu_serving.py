@@ -62,3 +62,36 @@ def test_served_results_equal_alone_runs(D, tight):
         assert d.admit_s >= d.arrival_s - 1e-9 and d.done_s > d.admit_s
     s = serving.summarize(done)
     assert s["requests"] == len(reqs) and s["p99_latency_s"] >= s["p50_latency_s"] > 0
+
+
+def test_autotuned_tiles_are_applied_and_results_equal_alone(D):
+    """The autotuner's table (threads per block, brick length per box-edge
+    class) reaches every admitted system, and each served result still equals
+    its alone run with the same launch shape, bit for bit."""
+    from paper_1804_06205_gb300 import autotune, serving
+    table = autotune.tune(edges=(8.0, 10.0), threads=(64, 128), beads=20_000, steps=3)
+    assert table["threads"] in (64, 128) and set(table["tiles"]) == {"8.0", "10.0"}
+    reqs = mini_stream()
+    srv = serving.Server(max_beads=10 ** 6, max_cells=10 ** 6, max_bonds=10 ** 5,
+                         max_systems=16, chunk=5, keep_states=True, table=table)
+    seen = {}
+    add = srv.batch.add_workload
+
+    def recording_add(w, step=0, tile_cells=0):
+        seen[id(w)] = tile_cells
+        return add(w, step=step, tile_cells=tile_cells)
+    srv.batch.add_workload = recording_add
+    done = srv.run(reqs)
+    srv.close()
+    assert len(done) == len(reqs)
+    for d in done:
+        r = reqs[d.rid]
+        want = serving.tile_for(table, r.workload.L)
+        assert want > 0 and seen[id(r.workload)] == want
+        g = D.System.from_workload(r.workload, precision=0, threads=table["threads"],
+                                   tile_cells=want)
+        g.set_state(r.workload.pos, r.workload.vel, 0)
+        g.step(r.steps)
+        ref = g.get_state()
+        g.close()
+        assert np.array_equal(d.state[0], ref[0]) and np.array_equal(d.state[1], ref[1])
