@@ -27,6 +27,8 @@ synthetic, seeded.  Prints ONE JSON line (rank 0):
           Poisson process, served by continuous batching; p50/p99 completion
           latency and throughput, after the autotuner picked the launch shape;
           serving_saturated: the same stream all arriving at once
+  launch_modes  ms/step with one launch per kernel vs one persistent
+          cooperative launch per call (small systems, a batch, fluid_3m)
   fp64_plain    the plain FP64 path, one system per launch (last in the line)
 
 --impl reference times the FP64 CPU oracle (the only reference: the paper
@@ -299,6 +301,42 @@ def alpha_helix_leg(D, W, stream):
             "kT": o["kT"], "p_total": o["p_total"]}
 
 
+def launch_modes_leg(D, W, stream, steps=400, warmup=20):
+    """ms/step of the one-launch-per-kernel path (programmatic dependent
+    launch) and of the persistent cooperative launch (one launch per call of
+    `steps` steps), FP32, on the small and batched workloads where launches
+    matter and on fluid_3m."""
+    import torch
+    cases = [("alpha_helix_24k", [W.alpha_helix_24k()]),
+             ("table1_5k", [W.camus_table(5000)]),
+             ("serving_batch_9", [W.serving_system(900 + k) for k in range(9)]),
+             ("fluid_3m", [W.fluid_3m()])]
+    out = {}
+    for name, ws in cases:
+        row = {"beads": int(sum(w.n for w in ws)), "systems": len(ws)}
+        st = steps if row["beads"] < 1_000_000 else 100
+        for persistent in (0, 1):
+            b = D.Batch(sum(w.n for w in ws), sum(int(np.prod(np.floor(w.L))) for w in ws),
+                        max(1, sum(w.nbonds for w in ws)), max_systems=len(ws),
+                        persistent=persistent, cuda_stream=stream.cuda_stream)
+            for w in ws:
+                b.add_workload(w)
+            b.step(warmup)
+            b.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0 = b.launch_count()
+            e0.record(stream)
+            b.step(st)
+            e1.record(stream)
+            e1.synchronize()
+            row["persistent_ms" if persistent else "direct_ms"] = e0.elapsed_time(e1) / st
+            row["persistent_launches" if persistent else "direct_launches"] = b.launch_count() - l0
+            b.close()
+        row["steps"] = st
+        out[name] = row
+    return out
+
+
 def serving_leg(args, stream, saturated=False, table=None):
     """Continuous batching of a stream of independent systems: Poisson
     arrivals at the workload's rate, or (saturated) all of them at t = 0."""
@@ -532,7 +570,9 @@ def main():
             forces["f64"] = f64
         err = oracle_force_error(w, forces, err_step)
 
-    serve = serve_sat = tables = helix = None
+    serve = serve_sat = tables = helix = modes = None
+    if ws == 1 and not args.no_extras:
+        modes = launch_modes_leg(D, W, stream)
     if ws == 1 and not args.no_serving:
         serve, table = serving_leg(args, stream)
         serve_sat, _ = serving_leg(args, stream, saturated=True, table=table)
@@ -554,7 +594,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks,
                 # bulky context first; the tail of the line keeps the key results
-                "paper_tables": tables, "alpha_helix": helix,
+                "paper_tables": tables, "alpha_helix": helix, "launch_modes": modes,
                 "serving_detail": serve, "serving_saturated_detail": serve_sat,
                 "pair_interactions_per_s": ws * pairs * args.steps / (ms32 * 1e-3),
                 "phases_ms": dict(zip(("update_sort", "pair", "bond_vel"), phases)),

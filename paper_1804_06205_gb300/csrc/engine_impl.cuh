@@ -935,8 +935,13 @@ class BatchEngine : public BatchBase {
 
     template <int T>
     int launch_persistent_t(const StepArgs<P> &sa) {
+        // as many blocks as the largest phase can use, at most the co-resident
+        // grid: the pair phase takes one brick per block at a time, the bead
+        // phases a few beads per thread
+        const int want = std::max({sa.nbricks, (sa.nbeads + 4 * T - 1) / (4 * T), sa.ntiles, 1});
+        const int grid = std::min(std::min(persist_grid_, want), BAR_GROUP * BAR_MAX_GROUPS);
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)persist_grid_);
+        cfg.gridDim = dim3((unsigned)grid);
         cfg.blockDim = dim3((unsigned)T);
         cfg.dynamicSmemBytes = smem_n_;
         cfg.stream = stream_;

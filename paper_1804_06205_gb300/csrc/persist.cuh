@@ -16,11 +16,19 @@
 
 namespace dpd {
 
-// Arrival counter and generation of the grid barrier (device memory, zeroed
-// by the host before each launch).
+// The grid barrier's words (device memory, zeroed by the host before each
+// launch): blocks arrive on the counter of their group of BAR_GROUP blocks,
+// the last arrival of a group on the top counter, and the last arrival there
+// advances the generation every waiting block polls.  `work` hands out the
+// pair phase's bricks.
+constexpr int BAR_GROUP = 32;
+constexpr int BAR_MAX_GROUPS = 256;
 struct GridBar {
-    unsigned int count;
+    unsigned int count[BAR_MAX_GROUPS];
+    unsigned int top;
     unsigned int gen;
+    unsigned int work;
+    unsigned int pad;
 };
 
 __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p) {
@@ -39,11 +47,22 @@ __device__ __forceinline__ bool grid_barrier(GridBar *bar, unsigned int nblocks,
         int ok = 1;
         const unsigned int g = ld_acquire_gpu(&bar->gen);
         __threadfence();   // this block's writes before its arrival
-        if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
-            atomicExch(&bar->count, 0u);
+        const unsigned int grp = blockIdx.x / BAR_GROUP;
+        const unsigned int ngroups = (nblocks + BAR_GROUP - 1) / BAR_GROUP;
+        const unsigned int gsize = min((unsigned int)BAR_GROUP, nblocks - grp * BAR_GROUP);
+        bool released = false;
+        if (atomicAdd(&bar->count[grp], 1u) == gsize - 1) {
+            // no block of this group can arrive again before the generation moves
+            atomicExch(&bar->count[grp], 0u);
             __threadfence();
-            atomicAdd(&bar->gen, 1u);   // release every waiting block
-        } else {
+            if (atomicAdd(&bar->top, 1u) == ngroups - 1) {
+                atomicExch(&bar->top, 0u);
+                __threadfence();
+                atomicAdd(&bar->gen, 1u);   // release every waiting block
+                released = true;
+            }
+        }
+        if (!released) {
             const long long t0 = clock64();
             while (ld_acquire_gpu(&bar->gen) == g) {
                 if (clock64() - t0 > budget) {
@@ -51,7 +70,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar *bar, unsigned int nblocks,
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
         __threadfence();
@@ -166,8 +185,20 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1)
         if (!sync()) return;
         for (int t = gt; t < a.nbeads; t += gstride) gather_one<P, false>(a.ga[p], t);
         if (!sync()) return;
-        for (int br = blockIdx.x; br < a.nbricks; br += nb)
-            if (!pair_brick<P, T, false, true>(a.pl, br)) return;   // ST_TIMEOUT is set
+        {   // bricks handed out one at a time (their costs vary with occupancy);
+            // the tickets of step k are [k (nbricks + nb), (k + 1) (nbricks + nb)):
+            // every brick once, then one ticket per block that finds none left
+            __shared__ int s_br;
+            const unsigned int base = (unsigned int)k * (unsigned int)(a.nbricks + (int)nb);
+            for (;;) {
+                if (threadIdx.x == 0) s_br = (int)(atomicAdd(&a.bar->work, 1u) - base);
+                __syncthreads();
+                const int br = s_br;
+                __syncthreads();
+                if (br >= a.nbricks) break;
+                if (!pair_brick<P, T, false, true>(a.pl, br)) return;   // ST_TIMEOUT is set
+            }
+        }
         if (!sync()) return;
         // bonds and velocity; every step but the last also makes the next
         // step's position update
