@@ -11,7 +11,8 @@ synthetic, seeded.  Prints ONE JSON line (rank 0):
   value   FP32 particle-steps/s, state resident in HBM, the step kernels
           launched directly (programmatic dependent launch) on one stream
   e2e     the same metric through the public API with host buffers: every
-          step sets the state from pinned host memory, steps, reads it back
+          step restores the full state (a checkpoint) from pinned host memory,
+          steps, and writes the new checkpoint back
   roofline    the pair kernel (dominant) against the plain-ALU issue peak,
           with the algorithmic operation count of the method per bead
   roofline_hbm_phases  cell division and bonds/velocity/update against the
@@ -500,29 +501,31 @@ def main():
                 "phases_ms": dict(zip(("update_sort", "pair", "bond_vel"), ph64)),
                 "fp32_speedup": value / v64}
 
-    # ---- end to end through the public API with pinned host buffers
+    # ---- end to end through the public API with pinned host buffers: every
+    # step takes its whole input state (a checkpoint: cell, offset, v, f per
+    # bead) from pinned host memory and returns the new one there
     g = D.System.from_workload(w, precision=D.DPD_FP32, cuda_stream=stream.cuda_stream)
-    pos_h = torch.from_numpy(np.ascontiguousarray(w.pos)).pin_memory()
-    vel_h = torch.from_numpy(np.ascontiguousarray(w.vel)).pin_memory()
-    g.set_state_ptr(pos_h.data_ptr(), vel_h.data_ptr(), 0)
+    g.set_state(w.pos, w.vel, 0)
+    nb = g.checkpoint_bytes()
+    ck_h = torch.empty(nb, dtype=torch.uint8).pin_memory()
+    g.get_checkpoint_ptr(ck_h.data_ptr(), nb)
     for _ in range(2):
+        g.set_checkpoint_ptr(ck_h.data_ptr(), nb)
         g.step(1)
-        g.get_state_ptr(pos_h.data_ptr(), vel_h.data_ptr())
+        g.get_checkpoint_ptr(ck_h.data_ptr(), nb)
     barrier()
     t0 = time.perf_counter()
-    step = 2
     for _ in range(args.e2e_steps):
-        g.set_state_ptr(pos_h.data_ptr(), vel_h.data_ptr(), step)
+        g.set_checkpoint_ptr(ck_h.data_ptr(), nb)
         g.step(1)
-        step = g.get_state_ptr(pos_h.data_ptr(), vel_h.data_ptr())
+        g.get_checkpoint_ptr(ck_h.data_ptr(), nb)
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     g.close()
     e2e = {"value": ws * w.n * args.e2e_steps / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": 2 * w.n * 3 * 8, "d2h_bytes_per_step": 2 * w.n * 3 * 8,
-           "steps": args.e2e_steps,
-           "note": "per step: dpd_set_state from pinned host (pos, vel), which evaluates f "
-                   "at the new state, dpd_step(1), dpd_get_state to pinned host (pos, vel)"}
+           "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb, "steps": args.e2e_steps,
+           "note": "per step: dpd_set_checkpoint from pinned host (the full state, 40 B per "
+                   "bead: cell, offset, v, f), dpd_step(1), dpd_get_checkpoint to pinned host"}
 
     # ---- roofline of the pair kernel (plain-ALU bound)
     pair_ms = phases[1]

@@ -207,8 +207,9 @@ int dpd_profile_end(dpd_handle *h, double ms[3], int64_t *nsteps);
  *   evaluation; the handle must have been created with the same parameters
  *   (precision, n, box and seed are checked against the header; types, a_ij,
  *   bonds and the integrator parameters are the caller's responsibility).
- *   Synchronises.  Errors: DPD_EINVAL (mismatched header, a cell key out of
- *   range, a non-finite value; the previous state is then lost), DPD_ECUDA. */
+ *   Synchronises.  Errors: DPD_EINVAL (mismatched header; or, found on the
+ *   device, a cell key out of range or a non-finite value, after which the
+ *   previous state is lost), DPD_ECUDA. */
 int dpd_checkpoint_bytes(const dpd_handle *h, int64_t *bytes);
 int dpd_get_checkpoint(dpd_handle *h, void *buf, int64_t bytes);
 int dpd_set_checkpoint(dpd_handle *h, const void *buf, int64_t bytes);

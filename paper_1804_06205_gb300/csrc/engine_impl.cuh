@@ -542,16 +542,6 @@ class BatchEngine : public BatchBase {
             return DPD_EINVAL;
         }
         const Rec *rec = reinterpret_cast<const Rec *>(static_cast<const char *>(buf) + sizeof(got));
-        if (P::kOffsets) {   // keys index the cell counts: check them before the device does
-            for (int i = 0; i < h.n; ++i) {
-                uint32_t k;
-                std::memcpy(&k, reinterpret_cast<const char *>(rec + i), sizeof(k));
-                if (k >= (uint32_t)h.ncell) {
-                    err_ = "checkpoint holds a cell key out of range";
-                    return DPD_EINVAL;
-                }
-            }
-        }
         if ((rc = ensure_io((size_t)h.n))) return rc;
         const int old = cur_ ^ 1;
         InitArgs<P> ia;
@@ -588,7 +578,7 @@ class BatchEngine : public BatchBase {
             st &= ~ST_BADINPUT;
             DPD_CU(cudaMemcpy(status_, &st, sizeof(int), cudaMemcpyHostToDevice));
             h.has_state = false;
-            err_ = "checkpoint holds a non-finite value";
+            err_ = "checkpoint holds a non-finite value or a cell key out of range";
             return DPD_EINVAL;
         }
         h.has_state = true;
@@ -1047,6 +1037,7 @@ class BatchEngine : public BatchBase {
         PairLaunch<P> &pl = sa.pl;
         pl.sys = sys_;
         pl.brick_sys = brick_sys_;
+        pl.sys1 = sys1();
         pl.br_lo = 0;
         pl.capmax = capmax_;
         pl.Xmax = xmax_;
@@ -1093,6 +1084,7 @@ class BatchEngine : public BatchBase {
         PairLaunch<P> pl;
         pl.sys = sys_;
         pl.brick_sys = brick_sys_;
+        pl.sys1 = sys1();
         pl.br_lo = br_lo;
         pl.capmax = capmax_;
         pl.Xmax = xmax_;

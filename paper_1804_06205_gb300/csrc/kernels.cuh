@@ -663,6 +663,7 @@ struct PairLaunch {   // a launch over bricks [br_lo, br_lo + gridDim.x) of any 
     using real = typename P::real;
     const SysDesc<P> *sys;
     const int *brick_sys;
+    int sys1;                           // the only system of a batch of one, else -1
     int br_lo;
     int capmax, Xmax;                   // shared-memory layout
     const vec4 *pos, *vt;
@@ -810,7 +811,7 @@ __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int br
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(32) unsigned char smem[];
     // this block's brick and system
-    const int sysi = la.brick_sys[brick];
+    const int sysi = la.sys1 >= 0 ? la.sys1 : la.brick_sys[brick];
     const SysDesc<P> &D = la.sys[sysi];
     PairArgs<P> a;
     a.pos = la.pos;
@@ -1238,40 +1239,42 @@ __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int br
                             // hit only (a row never holds more candidates than free
                             // levels, so the stores stay in the queue); the next pair
                             // of candidates is loaded before this pair is tested
+                            {
                             uint32_t ad = scan_u32 + 16u * (uint32_t)(q - c0);
                             const uint32_t ad_end = scan_u32 + 16u * (uint32_t)(qe - c0);
                             uint32_t ent = (uint32_t)(q - c0);
                             uint32_t qa = myq_u32 + 64u * (uint32_t)nh;
+                            // one candidate: its hit is 0 < r^2 < 1 (FP32: the bits of a
+                            // non-negative binary32 order like its value, so this is one
+                            // unsigned compare of the bits minus one) or binary32
+                            // r^2 < 1.001 and not the bead itself (FP64)
+                            auto hit = [&](const float4 &c, uint32_t e) -> bool {
+                                const float2 d = __fadd2_rn(make_float2(c.x, c.y), nxy);
+                                const float dzv = add_rn(c.z, nzs);
+                                const float r2 = fma_rn(dzv, dzv, fma_rn(d.y, d.y, mul_rn(d.x, d.x)));
+                                return P::kOffsets ? (__float_as_uint(r2) - 1u < 0x3F7FFFFFu)
+                                                   : (r2 < scan_lim && e != self);
+                            };
+                            auto put = [&](bool h, uint32_t e) {
+                                sts16(qa, e);
+                                qa += h ? 64u : 0u;
+                            };
+                            // two at a time, the next two loaded into the same registers
+                            // once the tests have read them
                             float4 pa = lds128(ad), pb = lds128(ad + 16u);
-                            while (ad + 16u < ad_end) {   // two at a time
-                                const float4 ca = pa, cb = pb;
+                            while (ad + 16u < ad_end) {
+                                const bool ha = hit(pa, ent), hb = hit(pb, ent + 1u);
                                 ad += 32u;
                                 pa = lds128(ad);
                                 pb = lds128(ad + 16u);
-                                const float2 da = __fadd2_rn(make_float2(ca.x, ca.y), nxy);
-                                const float2 db = __fadd2_rn(make_float2(cb.x, cb.y), nxy);
-                                const float az = add_rn(ca.z, nzs), bz = add_rn(cb.z, nzs);
-                                const float ra = fma_rn(az, az, fma_rn(da.y, da.y, mul_rn(da.x, da.x)));
-                                const float rb = fma_rn(bz, bz, fma_rn(db.y, db.y, mul_rn(db.x, db.x)));
-                                const bool ha = ra < scan_lim && (P::kOffsets ? ra > 0.0f : ent != self);
-                                const bool hb = rb < scan_lim && (P::kOffsets ? rb > 0.0f : ent + 1u != self);
-                                sts16(qa, ent);
-                                qa += ha ? 64u : 0u;
-                                sts16(qa, ent + 1u);
-                                qa += hb ? 64u : 0u;
+                                put(ha, ent);
+                                put(hb, ent + 1u);
                                 ent += 2u;
                             }
-                            if (ad < ad_end) {   // an odd last candidate (already loaded)
-                                const float2 d = __fadd2_rn(make_float2(pa.x, pa.y), nxy);
-                                const float dzv = add_rn(pa.z, nzs);
-                                const float r2 = fma_rn(dzv, dzv, fma_rn(d.y, d.y, mul_rn(d.x, d.x)));
-                                const bool h = r2 < scan_lim && (P::kOffsets ? r2 > 0.0f : ent != self);
-                                sts16(qa, ent);
-                                qa += h ? 64u : 0u;
-                                ++ent;
-                            }
+                            if (ad < ad_end) { put(hit(pa, ent), ent); ++ent; }
                             q = (int)ent + c0;
                             nh = (int)((qa - myq_u32) >> 6);
+                            }
                         }
                         if (q < qe_full) {
                             stopped = true;
@@ -1734,8 +1737,8 @@ __global__ void __launch_bounds__(256) k_ckpt_out(int s, const SysDesc<P> *sys,
     out[i] = r;
 }
 
-// Restore: like the initial binning (k_init), from checkpoint records (FP32
-// keys were checked against the cell count on the host).
+// Restore: like the initial binning (k_init), from checkpoint records; a
+// non-finite value or an FP32 key beyond the system's cells sets ST_BADINPUT.
 template <class P>
 __global__ void __launch_bounds__(256) k_ckpt_in(InitArgs<P> a,
                                                  const typename CkptRec<P>::type *rec) {
@@ -1752,6 +1755,10 @@ __global__ void __launch_bounds__(256) k_ckpt_in(InitArgs<P> a,
     if constexpr (P::kOffsets) {
         fin = fin && isfinite(r.o[0]) && isfinite(r.o[1]) && isfinite(r.o[2]);
         key = r.key;
+        if (key >= (uint32_t)D.ncell) {   // refused by the host after the sync; clamped so
+            fin = false;                  // that nothing reads or counts out of range
+            key = 0u;
+        }
         out = mk4<typename P::vec4, real>(r.o[0], r.o[1], r.o[2], P::pack_int(a.types[i]));
     } else {
         place_bead<P>(D, r.x[0], r.x[1], r.x[2], P::pack_int(a.types[i]), out, key, a.status,

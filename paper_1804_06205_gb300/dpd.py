@@ -313,6 +313,20 @@ class System:
         self._check(lib.dpd_set_checkpoint(self.h, C.c_char_p(data), len(data)),
                     "dpd_set_checkpoint")
 
+    def checkpoint_bytes(self) -> int:
+        nb = C.c_int64(0)
+        self._check(lib.dpd_checkpoint_bytes(self.h, C.byref(nb)), "dpd_checkpoint_bytes")
+        return nb.value
+
+    def get_checkpoint_ptr(self, ptr, nbytes):
+        """The checkpoint into host memory at ptr (e.g. a pinned buffer)."""
+        self._check(lib.dpd_get_checkpoint(self.h, C.c_void_p(ptr), int(nbytes)),
+                    "dpd_get_checkpoint")
+
+    def set_checkpoint_ptr(self, ptr, nbytes):
+        self._check(lib.dpd_set_checkpoint(self.h, C.c_void_p(ptr), int(nbytes)),
+                    "dpd_set_checkpoint")
+
     def sync(self):
         self._check(lib.dpd_sync(self.h), "dpd_sync")
 
