@@ -148,6 +148,8 @@ class BatchEngine : public BatchBase {
 
     // ------------------------------------------------------------ membership
     int add_system(const Config &c, int *slot) override {
+        int rc0 = flush_removals();
+        if (rc0) return rc0;
         int s = -1;
         for (int k = 0; k < NS_; ++k)
             if (!hs_[k].live) {
@@ -192,18 +194,29 @@ class BatchEngine : public BatchBase {
         return DPD_OK;
     }
 
+    // Removal frees the slot at once; the survivors are re-packed (one
+    // relayout for any number of removals) before the next step or admission.
     int remove_system(int s) override {
         if (s < 0 || s >= NS_ || !hs_[s].live) return DPD_EINVAL;
+        hs_[s].live = false;
+        order_.erase(std::find(order_.begin(), order_.end(), s));
+        repack_pending_ = true;
+        return DPD_OK;
+    }
+
+    int flush_removals() {
+        if (!repack_pending_) return DPD_OK;
+        repack_pending_ = false;
         int rc = check_status();
         if (rc) return rc;
         std::vector<int> old0(NS_, 0);
         for (int k : order_) old0[k] = hs_[k].bead0;
-        hs_[s].live = false;
-        order_.erase(std::find(order_.begin(), order_.end(), s));
-        // re-pack the survivors in order
+        // re-pack the survivors in order; only systems that moved are uploaded
         used_beads_ = used_cells_ = used_bricks_ = used_bonds_ = 0;
         for (int k : order_) {
             SysHost &h = hs_[k];
+            const bool moved = h.bead0 != used_beads_ || h.cell0 != used_cells_ ||
+                               h.brick0 != used_bricks_ || h.bond0 != used_bonds_;
             h.bead0 = used_beads_;
             h.cell0 = used_cells_;
             h.brick0 = used_bricks_;
@@ -212,7 +225,7 @@ class BatchEngine : public BatchBase {
             used_cells_ += h.ncell;
             used_bricks_ += h.nbrick;
             used_bonds_ += h.nbond;
-            if ((rc = upload_system(k))) return rc;
+            if (moved && (rc = upload_system(k, false))) return rc;
         }
         if ((rc = rebuild_reduce_maps()) || (rc = update_smem())) return rc;
         if (used_beads_ > 0) {
@@ -240,7 +253,8 @@ class BatchEngine : public BatchBase {
             std::swap(key_, key_tmp_);
             cur_ ^= 1;
         }
-        DPD_CU(cudaStreamSynchronize(stream_));
+        DPD_CU(cudaStreamSynchronize(stream_));   // also releases the upload staging
+        upload_keep_.clear();
         drop_graphs();
         return DPD_OK;
     }
@@ -314,6 +328,8 @@ class BatchEngine : public BatchBase {
 
     int step(int64_t nsteps) override {
         if (nsteps < 0) return DPD_EINVAL;
+        int rc0 = flush_removals();
+        if (rc0) return rc0;
         if (order_.empty()) return nsteps == 0 ? DPD_OK : DPD_ENOSTATE;
         for (int k : order_)
             if (!hs_[k].has_state) return DPD_ENOSTATE;
@@ -619,10 +635,13 @@ class BatchEngine : public BatchBase {
     }
 
     void usage(int64_t used[4], int64_t cap[4]) const override {
-        used[0] = used_beads_;
-        used[1] = used_cells_;
-        used[2] = used_bricks_;
-        used[3] = used_bonds_;
+        used[0] = used[1] = used[2] = used[3] = 0;   // the live systems (re-packed or not)
+        for (int k : order_) {
+            used[0] += hs_[k].n;
+            used[1] += hs_[k].ncell;
+            used[2] += hs_[k].nbrick;
+            used[3] += hs_[k].nbond;
+        }
         cap[0] = NB_;
         cap[1] = NC_;
         cap[2] = NBR_;
@@ -745,7 +764,7 @@ class BatchEngine : public BatchBase {
 
     // Descriptor, bead -> system and brick -> system maps, a_ij table and
     // bond records of system s at its current place in the pools.
-    int upload_system(int s) {
+    int upload_system(int s, bool sync = true) {
         SysHost &h = hs_[s];
         const Config &c = h.cfg;
         SysDesc<P> &d = hsys_[s];
@@ -819,8 +838,14 @@ class BatchEngine : public BatchBase {
             DPD_CU(cudaMemcpyAsync(bpar_ + h.bond0, par.data(), nb * sizeof(vec4),
                                    cudaMemcpyHostToDevice, stream_));
         }
-        // the host vectors above must outlive the asynchronous copies
-        DPD_CU(cudaStreamSynchronize(stream_));
+        // the host buffers above must outlive the asynchronous copies: wait now,
+        // or keep them until the caller's next synchronisation
+        if (sync) {
+            DPD_CU(cudaStreamSynchronize(stream_));
+        } else {
+            upload_keep_.push_back(std::make_shared<UploadBufs>(std::move(a), std::move(bp),
+                                                                std::move(par)));
+        }
         return DPD_OK;
     }
 
@@ -1390,6 +1415,15 @@ class BatchEngine : public BatchBase {
     real *atab_ = nullptr;
     int32_t *bptr_ = nullptr, *bpartner_ = nullptr;
     vec4 *bpar_ = nullptr;
+    struct UploadBufs {   // host data of an upload whose copies are in flight
+        UploadBufs(std::vector<real> &&a_, std::vector<int32_t> &&b_, std::vector<vec4> &&p_)
+            : a(std::move(a_)), bp(std::move(b_)), par(std::move(p_)) {}
+        std::vector<real> a;
+        std::vector<int32_t> bp;
+        std::vector<vec4> par;
+    };
+    std::vector<std::shared_ptr<UploadBufs>> upload_keep_;
+    bool repack_pending_ = false;
     GridBar *bar_ = nullptr;               // the persistent kernel's grid barrier
     int persist_grid_ = 0;                 // its co-resident grid (0: not available)
     // clock cycles a block of the persistent kernel waits at one grid barrier
