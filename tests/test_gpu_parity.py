@@ -109,13 +109,19 @@ def test_cells_bitexact_after_steps_fp64(D):
     assert np.array_equal(start, ostart)
 
 
-def test_cells_invariants_after_steps_fp32(D):
+def test_cells_after_steps_fp32(D):
+    """After steps the FP32 path's cell index is state (the integer cell and a
+    binary32 offset in [0, h), moved by whole cells), not re-derived from an
+    FP64 position.  Its keys must equal the oracle's key of that same state --
+    x = c h + o formed in FP64 from the checkpoint's exact cell and offset --
+    for every bead whose x is not within FP64 rounding of a cell face; there
+    the two may differ by one cell, and no further."""
     w = WL["odd_box"]
     g = gsys(D, w, FP32)
     g.set_state(w.pos, w.vel, 0)
     g.step(25)
-    pos, _, _, _ = g.get_state()
     key, order, start = g.cells()
+    ck = g.get_checkpoint()
     nc = g.nc
     assert sorted(order.tolist()) == list(range(w.n))
     ks = key[order].astype(np.int64)
@@ -123,13 +129,21 @@ def test_cells_invariants_after_steps_fp32(D):
     assert np.all(np.diff(order)[np.diff(ks) == 0] > 0)
     assert np.array_equal(np.diff(start), np.bincount(key.astype(np.int64),
                                                       minlength=int(np.prod(nc))))
-    # the key agrees with the oracle's key of the returned position except for
-    # beads within FP32 rounding of a cell face
-    okey = O.cell_keys(osys(w), pos)
+    rec = np.frombuffer(ck, dtype=np.dtype([("key", "<u4"), ("o", "<f4", 3), ("v", "<f4", 3),
+                                            ("f", "<f4", 3)]), offset=80)
+    assert np.array_equal(rec["key"], key)
     h = w.L / nc
-    frac = pos / h - np.floor(pos / h)
-    near = np.any((frac < 1e-5) | (frac > 1 - 1e-5), axis=1)
+    c = np.stack([key % nc[0], (key // nc[0]) % nc[1], key // (nc[0] * nc[1])], axis=1)
+    o = rec["o"].astype(np.float64)
+    assert np.all((o >= 0.0) & (o < h))
+    x = c * h + o
+    okey = O.cell_keys(osys(w), x)
+    frac = x / h - np.floor(x / h)
+    near = np.any((frac < 1e-12) | (frac > 1.0 - 1e-12), axis=1)
     assert np.array_equal(key[~near], okey[~near])
+    oc = np.stack([okey % nc[0], (okey // nc[0]) % nc[1], okey // (nc[0] * nc[1])], axis=1)
+    dcell = np.abs(c - oc.astype(np.int64))
+    assert np.all(np.minimum(dcell, nc - dcell)[near] <= 1)
 
 
 # ------------------------------------------------------------------ forces
