@@ -1121,33 +1121,53 @@ __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int br
                     // so every kernel variant rounds the sums the same way
                     const float2 nip = make_float2(-ip.x, -ip.y), niv = make_float2(-iv.x, -iv.y);
                     float2 ns = make_float2(0.0f - sx, 0.0f - sy);
-                    for (int m = 0; m < nmax; ++m) {
+                    // one queue entry: the pair's magnitude and the unit vector from
+                    // i to j (x, y packed), and the sampled terms
+                    auto term = [&](int jl, float &mag, float2 &e, float &ez, float &rr1,
+                                    float &fc, float &w) {
+                        const vec4 pj = s_pos[jl], vj = s_vt[jl];
+                        const float2 d = __fadd2_rn(make_float2(pj.x, pj.y), nip);
+                        const float dzv = pj.z - ip.z;
+                        const float r2 = fma_rn(dzv, dzv, fma_rn(d.y, d.y, mul_rn(d.x, d.x)));
+                        const float rinv = rsqrt_r(r2);
+                        rr1 = mul_rn(r2, rinv);
+                        w = 1.0f - rr1;
+                        e = __fmul2_rn(d, make_float2(rinv, rinv));
+                        ez = mul_rn(dzv, rinv);
+                        const float2 dv = __fadd2_rn(make_float2(vj.x, vj.y), niv);
+                        const float evel = fma_rn(ez, vj.z - iv.z, fma_rn(e.y, dv.y, mul_rn(e.x, dv.x)));
+                        const float aij = s_a[P::unpack_int(ip.w) * nt + P::unpack_int(pj.w)];
+                        const int32_t idi = P::unpack_int(iv.w), idj = P::unpack_int(vj.w);
+                        const uint32_t lo = (uint32_t)min(idi, idj), hi = (uint32_t)max(idi, idj);
+                        const uint2 rnd = philox_rk(lo, hi, s_lo, s_hi, rkl);
+                        const float th = theta_pair(rnd, a.noise, 0.0f, la.lntab);
+                        fc = mul_rn(aij, w);
+                        const float gw2 = mul_rn(mul_rn(a.gamma, w), w);
+                        mag = fma_rn(mul_rn(a.sig_sqdt, w), th, fma_rn(-gw2, evel, fc));
+                    };
+                    // two entries per iteration, independent until they are added in order
+                    for (int m = 0; m < nmax; m += 2) {
                         if (m < n) {
-                            const int jl = qb[m * 32 + col];
-                            const vec4 pj = s_pos[jl], vj = s_vt[jl];
-                            const float2 d = __fadd2_rn(make_float2(pj.x, pj.y), nip);
-                            const float dzv = pj.z - ip.z;
-                            const float r2 = fma_rn(dzv, dzv, fma_rn(d.y, d.y, mul_rn(d.x, d.x)));
-                            const float rinv = rsqrt_r(r2);
-                            const float rr1 = mul_rn(r2, rinv);
-                            const float w = 1.0f - rr1;
-                            const float2 e = __fmul2_rn(d, make_float2(rinv, rinv));
-                            const float ez = mul_rn(dzv, rinv);
-                            const float2 dv = __fadd2_rn(make_float2(vj.x, vj.y), niv);
-                            const float evel = fma_rn(ez, vj.z - iv.z, fma_rn(e.y, dv.y, mul_rn(e.x, dv.x)));
-                            const float aij = s_a[P::unpack_int(ip.w) * nt + P::unpack_int(pj.w)];
-                            const int32_t idi = P::unpack_int(iv.w), idj = P::unpack_int(vj.w);
-                            const uint32_t lo = (uint32_t)min(idi, idj), hi = (uint32_t)max(idi, idj);
-                            const uint2 rnd = philox_rk(lo, hi, s_lo, s_hi, rkl);
-                            const float th = theta_pair(rnd, a.noise, 0.0f, la.lntab);
-                            const float fc = mul_rn(aij, w);
-                            const float gw2 = mul_rn(mul_rn(a.gamma, w), w);
-                            const float mag = fma_rn(mul_rn(a.sig_sqdt, w), th, fma_rn(-gw2, evel, fc));
-                            ns = __ffma2_rn(make_float2(mag, mag), e, ns);
-                            sz = __fmaf_rn(-mag, ez, sz);
+                            const bool two = m + 1 < n;
+                            const int j0 = qb[m * 32 + col];
+                            const int j1 = two ? (int)qb[(m + 1) * 32 + col] : j0;
+                            float mag0, ez0, rr0, fc0, w0, mag1, ez1, rr1_, fc1, w1;
+                            float2 e0, e1;
+                            term(j0, mag0, e0, ez0, rr0, fc0, w0);
+                            term(j1, mag1, e1, ez1, rr1_, fc1, w1);
+                            ns = __ffma2_rn(make_float2(mag0, mag0), e0, ns);
+                            sz = __fmaf_rn(-mag0, ez0, sz);
                             if (SAMPLE) {
-                                sw += rr1 * fc;
-                                se += 0.5f * fc * w;
+                                sw += rr0 * fc0;
+                                se += 0.5f * fc0 * w0;
+                            }
+                            if (two) {
+                                ns = __ffma2_rn(make_float2(mag1, mag1), e1, ns);
+                                sz = __fmaf_rn(-mag1, ez1, sz);
+                                if (SAMPLE) {
+                                    sw += rr1_ * fc1;
+                                    se += 0.5f * fc1 * w1;
+                                }
                             }
                         }
                     }
