@@ -807,7 +807,6 @@ template <class P, int T, bool SAMPLE, bool REUSE = false>
 __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int brick) {
     using real = typename P::real;
     using vec4 = typename P::vec4;
-    constexpr int NW = T / 32;
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(32) unsigned char smem[];
     // this block's brick and system
@@ -879,7 +878,29 @@ __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int br
     // The (row, cell) grid of the neighbourhood is shared by all threads; a
     // thread's position in it advances by T without any division.
     const int gr0 = tid / W, gk0 = tid - gr0 * W, gdr = T / W, gdk = T - gdr * W;
-    if (tid < NRe) {   // each staged row's first key (wrapped y, z) and frame shift
+    // A staged row of X + 2 cells (k = 0..Xe+1 <-> ux = -1..Xe) is at most three
+    // contiguous source runs, split where x wraps: at k = 1 when x0 = 0, and
+    // where x0 + k - 1 = nx.  Run j covers cells [kb_j, kb_{j+1}), kb_0 = 0;
+    // -1: no such run.
+    const int kw = a.nx - x0 + 1;
+    const bool w1 = x0 == 0, w2 = kw <= Xe + 1;
+    const int kend = Xe + 2;
+    const int kb1 = w1 ? 1 : (w2 ? kw : kend);
+    const int kb2 = w1 ? (w2 ? kw : kend) : (w2 ? kend : -1);
+    const int kb3 = (w1 && w2) ? kend : -1;
+    auto run_of = [&](int k) { return k >= kb1 ? ((kb2 >= 0 && k >= kb2) ? 2 : 1) : 0; };
+    auto wrap_x = [&](int k) {   // the periodic x of staged cell k
+        const int xx = x0 + k - 1;
+        return xx + (xx < 0 ? a.nx : (xx >= a.nx ? -a.nx : 0));
+    };
+    auto row_key = [&](int r) {   // key of the (wrapped) staged row's cell x = 0
+        const int uy = r % SY - 1, uz = r / SY - 1;
+        int yy = y0 + uy, zz = z0 + uz;
+        yy += yy < 0 ? a.ny : (yy >= a.ny ? -a.ny : 0);
+        zz += zz < 0 ? a.nz : (zz >= a.nz ? -a.nz : 0);
+        return ((uint32_t)zz * a.ny + yy) * a.nx;
+    };
+    if (tid < NRe) {   // each staged row's first key and frame shift
         const int r = tid;
         const int uy = r % SY - 1, uz = r / SY - 1;
         int yy = y0 + uy, zz = z0 + uz;
@@ -897,106 +918,47 @@ __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int br
         s_rsh[2 * r] = sy;
         s_rsh[2 * r + 1] = sz;
     }
-    __syncthreads();
-    // per staged cell: counts (k = 0..Xe+1 <-> ux = -1..Xe), k = Xe+2 is the row end;
-    // the threads share the flattened (row, cell) grid, so that many cell-start
-    // loads are in flight at once
-    {
-        int r = gr0, k = gk0;
-#pragma unroll 2
-        for (int e = tid; e < NRe * W; e += T) {
-            int cnt = 0, first = 0;
-            if (k <= Xe + 1) {
-                int xx = x0 + k - 1;
-                xx += xx < 0 ? a.nx : (xx >= a.nx ? -a.nx : 0);
-                const uint32_t c = (uint32_t)s_rkey[r] + (uint32_t)xx;
-                first = (int)a.cell_start[c];
-                cnt = (int)a.cell_start[c + 1] - first;
-            }
-            s_cs[e] = cnt;
-            s_src[e] = first;
-            k += gdk;
-            r += gdr;
-            if (k >= W) {
-                k -= W;
-                ++r;
-            }
+    if (tid < NRe * 3) {   // run j of row r: its source range, from two cell starts
+        const int r = tid / 3, j = tid - 3 * r;
+        const int k0 = j == 0 ? 0 : (j == 1 ? kb1 : kb2);
+        const int k1 = j == 0 ? kb1 : (j == 1 ? kb2 : kb3);
+        int src = 0, len = 0;
+        if (k1 > k0) {
+            const uint32_t rk = row_key(r);
+            src = (int)a.cell_start[rk + (uint32_t)wrap_x(k0)];
+            len = (int)a.cell_start[rk + (uint32_t)wrap_x(k1 - 1) + 1u] - src;
         }
+        s_pc[tid * PAIR_PC] = src;        // first source slot
+        s_pc[tid * PAIR_PC + 2] = len;    // length
     }
     __syncthreads();
-    if (tid < 32) {   // exclusive scan of the counts: staged start of each cell
-        int carry = 0;
-        const int tot = NRe * W;
-        for (int b = 0; b < tot; b += 32) {
-            const int v = (b + tid < tot) ? s_cs[b + tid] : 0;
-            int inc = v;
+    __shared__ int s_total;
+    if (tid < 32) {   // first staged slot of each run: exclusive scan over the runs in order
+        const int n3 = NRe * 3;   // at most 48
+        const int v0 = tid < n3 ? s_pc[tid * PAIR_PC + 2] : 0;
+        const int v1 = tid + 32 < n3 ? s_pc[(tid + 32) * PAIR_PC + 2] : 0;
+        int i0 = v0, i1 = v1;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int u = __shfl_up_sync(FULL, inc, o);
-                if (tid >= o) inc += u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u0 = __shfl_up_sync(FULL, i0, o), u1 = __shfl_up_sync(FULL, i1, o);
+            if (tid >= o) {
+                i0 += u0;
+                i1 += u1;
             }
-            if (b + tid < tot) s_cs[b + tid] = carry + inc - v;
-            carry += __shfl_sync(FULL, inc, 31);
         }
+        const int t0 = __shfl_sync(FULL, i0, 31);
+        if (tid < n3) s_pc[tid * PAIR_PC + 1] = i0 - v0;
+        if (tid + 32 < n3) s_pc[(tid + 32) * PAIR_PC + 1] = t0 + i1 - v1;
+        if (tid == 31) s_total = t0 + i1;
     }
     __syncthreads();
-    if (tid < NRe) {   // contiguous source runs of each staged row, split where x wraps:
-        const int r = tid;   // at k = 1 when x0 = 0, and where x0 + k - 1 = nx
-        const int kw = a.nx - x0 + 1;
-        const bool w1 = x0 == 0, w2 = kw <= Xe + 1;
-        const int kend = Xe + 2;
-        // run j covers cells [kb_j, kb_{j+1}); -1: no such run
-        const int kb1 = w1 ? 1 : (w2 ? kw : kend);
-        const int kb2 = w1 ? (w2 ? kw : kend) : (w2 ? kend : -1);
-        const int kb3 = (w1 && w2) ? kend : -1;
-        auto put = [&](int j, int k0, int k1) {
-            int *pc = s_pc + (r * 3 + j) * PAIR_PC;
-            if (k1 >= 0) {
-                pc[0] = s_src[r * W + k0];                     // first source slot
-                pc[1] = s_cs[r * W + k0];                      // first staged slot
-                pc[2] = s_cs[r * W + k1] - s_cs[r * W + k0];   // length
-            } else {
-                pc[2] = 0;
-            }
-        };
-        put(0, 0, kb1);
-        put(1, kb1, kb2);
-        put(2, kb2, kb3);
-    }
-    if (tid < 4) {     // home rows (ry, rz) = (tid % 2, tid / 2)
-        const int ry = tid % 2, rz = tid / 2;
-        int hcount = 0, first = 0, gfirst = 0, sr = 0;
-        if (ry < BYe && rz < BZe) {
-            sr = (ry + 1) + SY * (rz + 1);
-            gfirst = s_src[sr * W + 1];
-            hcount = s_cs[sr * W + Xe + 1] - s_cs[sr * W + 1];
-        }
-        s_hr[4 * tid] = sr;
-        s_hr[4 * tid + 1] = first;
-        s_hr[4 * tid + 2] = hcount;
-        s_hr[4 * tid + 3] = gfirst;
-    }
-    __syncthreads();
-    if (tid == 0) {    // home rows' positions in the concatenated home list
-        int run = 0;
-        for (int h = 0; h < 4; ++h) {
-            s_hr[4 * h + 1] = run;
-            run += s_hr[4 * h + 2];
-        }
-    }
-    __syncthreads();
-
-    const int S = s_cs[NRe * W - 1];
-    const int H = s_hr[13] + s_hr[14];
-    const long long sctr = *a.counter;
-    const uint32_t s_lo = (uint32_t)(unsigned long long)sctr;
-    const uint32_t s_hi = (uint32_t)((unsigned long long)sctr >> 32);
-    const int nt = a.ntypes;
-    uint16_t *my_q = s_q + wid * PAIR_HMAX * 32;
-    // Stage slots [c0, c1) of the neighbourhood: bulk copies of each source run,
-    // then every staged cell moved into the brick's frame.  False if a copy
-    // never completed (the block must then leave).
-    auto stage = [&](int c0, int c1) -> bool {
+    const int S = s_total;
+    const int c1_first = min(S, cap);
+    // Staging of slots [c0, c1) of the neighbourhood, in two parts.  issue: bulk
+    // copies of each source run (positions, v~) onto the mbarrier.  complete:
+    // wait for them, then move every staged cell into the brick's frame.  False
+    // if a copy never completed (the block must then leave).
+    auto issue = [&](int c0, int c1) {
         fence_proxy_async_smem();   // this chunk's reads before the next copies
         __syncthreads();            // everyone is done with the previous chunk
         if (tid < NRe * 3) {        // one thread per source run: positions, v~
@@ -1010,7 +972,9 @@ __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int br
                 bulk_g2s(s_vt + (lo - c0), a.vt + src + (lo - dst), bytes, &s_mbar);
             }
         }
-        __syncthreads();
+    };
+    auto complete = [&](int c0, int c1) -> bool {
+        __syncthreads();            // every copy issued before the arrival
         if (tid == 0) mbar_arrive(&s_mbar);
         const bool got = mbar_wait_bounded(&s_mbar, mphase, MBAR_TRIES);
         mphase ^= 1u;
@@ -1055,6 +1019,66 @@ __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int br
         __syncthreads();   // staged and moved before anyone scans
         return true;
     };
+    // The first chunk's copies are in flight while the staged start of every
+    // cell (k = Xe+2: the row end) is formed from its run's staged start and
+    // its own cell start.
+    issue(0, c1_first);
+    bool first_pending = true;
+    {
+        int r = gr0, k = gk0;
+#pragma unroll 2
+        for (int e = tid; e < NRe * W; e += T) {
+            int st;
+            if (k <= Xe + 1) {
+                const int *pc = s_pc + (r * 3 + run_of(k)) * PAIR_PC;
+                st = pc[1] + (int)a.cell_start[(uint32_t)s_rkey[r] + (uint32_t)wrap_x(k)] - pc[0];
+            } else {
+                const int *pe = s_pc + (r * 3 + 2) * PAIR_PC;
+                st = pe[1] + pe[2];
+            }
+            s_cs[e] = st;
+            k += gdk;
+            r += gdr;
+            if (k >= W) {
+                k -= W;
+                ++r;
+            }
+        }
+    }
+    __syncthreads();
+    if (tid < 4) {     // home rows (ry, rz) = (tid % 2, tid / 2)
+        const int ry = tid % 2, rz = tid / 2;
+        int hcount = 0, first = 0, gfirst = 0, sr = 0;
+        if (ry < BYe && rz < BZe) {
+            sr = (ry + 1) + SY * (rz + 1);
+            const int *pc = s_pc + (sr * 3 + run_of(1)) * PAIR_PC;
+            gfirst = pc[0] + s_cs[sr * W + 1] - pc[1];    // global slot of cell k = 1's first bead
+            hcount = s_cs[sr * W + Xe + 1] - s_cs[sr * W + 1];
+        }
+        s_hr[4 * tid] = sr;
+        s_hr[4 * tid + 1] = first;
+        s_hr[4 * tid + 2] = hcount;
+        s_hr[4 * tid + 3] = gfirst;
+    }
+    __syncthreads();
+    if (tid == 0) {    // home rows' positions in the concatenated home list
+        int run = 0;
+        for (int h = 0; h < 4; ++h) {
+            s_hr[4 * h + 1] = run;
+            run += s_hr[4 * h + 2];
+        }
+    }
+    __syncthreads();
+    const int H = s_hr[13] + s_hr[14];
+    const long long sctr = *a.counter;
+    const uint32_t s_lo = (uint32_t)(unsigned long long)sctr;
+    const uint32_t s_hi = (uint32_t)((unsigned long long)sctr >> 32);
+    const int nt = a.ntypes;
+    uint16_t *my_q = s_q + wid * PAIR_HMAX * 32;
+    auto stage = [&](int c0, int c1) -> bool {
+        issue(c0, c1);
+        return complete(c0, c1);
+    };
     int staged_lo = -1;
     // FP64: balanced evaluation (ranks in s_src, which holds PAIR_NR * (Xmax + 3) ints)
     const bool balance = !P::kOffsets && PAIR_NR * (la.Xmax + 3) >= T;
@@ -1074,7 +1098,12 @@ __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int br
         const vec4 pr = a.pos[g], hv = a.vt[g];
         const uint32_t kg = a.key[g];
         if (staged_lo != 0) {
-            if (!stage(0, min(S, cap))) return false;
+            if (first_pending) {
+                if (!complete(0, c1_first)) return false;
+                first_pending = false;
+            } else if (!stage(0, c1_first)) {
+                return false;
+            }
             staged_lo = 0;
         }
         int uxi = 0;
@@ -1378,6 +1407,9 @@ __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int br
         }
         __syncwarp();
     }
+    // no home bead: the first chunk's copies must still land before the block
+    // leaves or reuses its shared memory
+    if (first_pending && !complete(0, c1_first)) return false;
     if (REUSE) {
         __syncthreads();
         if (tid == 0) mbar_inval(&s_mbar);
