@@ -1282,12 +1282,12 @@ __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int br
                             }
                             qe = q + PAIR_HMAX;                  // a crowded row: part of it
                         }
-                        {   // queue [level][lane]: the staged slot of each hit.  Shared
-                            // addresses are 32-bit window offsets; every candidate is
-                            // stored at the lane's next free level, which advances on a
-                            // hit only (a row never holds more candidates than free
-                            // levels, so the stores stay in the queue); the next pair
-                            // of candidates is loaded before this pair is tested
+                        {   // queue [level][lane]: the staged slot of each hit, stored
+                            // at the lane's next free level (a row never holds more
+                            // candidates than free levels, so the stores stay in the
+                            // queue).  Shared addresses are 32-bit window offsets; the
+                            // next pair of candidates is loaded before this pair is
+                            // tested
                             {
                             uint32_t ad = scan_u32 + 16u * (uint32_t)(q - c0);
                             const uint32_t ad_end = scan_u32 + 16u * (uint32_t)(qe - c0);
@@ -1305,8 +1305,10 @@ __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int br
                                                    : (r2 < scan_lim && e != self);
                             };
                             auto put = [&](bool h, uint32_t e) {
-                                sts16(qa, e);
-                                qa += h ? 64u : 0u;
+                                if (h) {
+                                    sts16(qa, e);
+                                    qa += 64u;
+                                }
                             };
                             // two at a time, the next two loaded into the same registers
                             // once the tests have read them
