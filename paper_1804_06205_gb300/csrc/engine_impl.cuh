@@ -111,7 +111,7 @@ class BatchEngine : public BatchBase {
         int rc;
         if ((rc = alloc(&pos_, N)) || (rc = alloc(&pos_tmp_, N)) || (rc = alloc(&vel_[0], N)) ||
             (rc = alloc(&vel_[1], N)) || (rc = alloc(&frc_[0], N)) || (rc = alloc(&frc_[1], N)) ||
-            (rc = alloc(&vt_, N)) || (rc = alloc(&fpair_, N)) || (rc = alloc(&ev_, N)) ||
+            (rc = alloc(&vt_, N)) || (rc = alloc(&ev_, N)) ||
             (rc = alloc(&key_, N)) || (rc = alloc(&key_tmp_, N)) || (rc = alloc(&rank_, N)) ||
             (rc = alloc(&src_, N)) || (rc = alloc(&sid_, N)) || (rc = alloc(&id_[0], N)) ||
             (rc = alloc(&id_[1], N)) || (rc = alloc(&inv_perm_, N)) || (rc = alloc(&bsys_, N)) ||
@@ -307,7 +307,7 @@ class BatchEngine : public BatchBase {
         DPD_CU(cudaMemcpyAsync(counter_ + s, &sv, sizeof(long long), cudaMemcpyHostToDevice,
                                stream_));
         if ((rc = enqueue_sort(h.bead0, h.bead0 + h.n, h.cell0, h.cell0 + h.ncell, old, cur_)) ||
-            (rc = launch_pair(false, h.brick0, h.nbrick)) ||
+            (rc = launch_pair(false, h.brick0, h.nbrick, frc_[cur_])) ||
             (rc = enqueue_bonds(true, false, h.bead0, h.bead0 + h.n)))
             return rc;
         h.obs_fresh = false;
@@ -413,7 +413,9 @@ class BatchEngine : public BatchBase {
         if (!h.obs_fresh) {   // the sampled pair sums and the bond sums of this state
             int rc = check_status();
             if (rc) return rc;
-            if ((rc = launch_pair(true, h.brick0, h.nbrick)) ||
+            // the forces go to the other buffer, free between steps; only the
+            // sampled sums are kept
+            if ((rc = launch_pair(true, h.brick0, h.nbrick, frc_[cur_ ^ 1])) ||
                 (h.nbond > 0 && (rc = enqueue_bonds(false, false, h.bead0, h.bead0 + h.n,
                                                     false, true))) ||
                 (rc = enqueue_reduce(h.red0, h.nred, h.rsys_index, 1, false)))
@@ -1037,7 +1039,7 @@ class BatchEngine : public BatchBase {
             ba.b_hi = used_beads_;
             ba.sys = sys_;
             ba.bsys = bsys_;
-            ba.fpair = fpair_;
+            ba.fpair = frc_[nxt];   // the pair phase writes the new force buffer
             ba.pos = pos_;
             ba.key = key_;
             ba.id = id_[nxt];
@@ -1059,7 +1061,7 @@ class BatchEngine : public BatchBase {
             ba.counter = counter_;
             ba.status = status_;
         }
-        PairLaunch<P> &pl = sa.pl;
+        PairLaunch<P> &pl = sa.pl[0];
         pl.sys = sys_;
         pl.brick_sys = brick_sys_;
         pl.sys1 = sys1();
@@ -1072,11 +1074,12 @@ class BatchEngine : public BatchBase {
         pl.vt = vt_;
         pl.key = key_;
         pl.cell_start = cell_start_;
-        pl.fpair = fpair_;
         pl.ev = ev_;
         pl.atab = atab_;
         pl.counter = counter_;
         pl.status = status_;
+        sa.pl[1] = pl;
+        for (int p = 0; p < 2; ++p) sa.pl[p].fpair = sa.bo[p].frc;   // into the step's force buffer
         sa.count = count_;
         sa.bsum = bsum_;
         sa.cell_start = cell_start_;
@@ -1104,7 +1107,8 @@ class BatchEngine : public BatchBase {
         return DPD_OK;
     }
 
-    int launch_pair(bool sample, int br_lo, int nbr) {
+    // pair forces of bricks [br_lo, br_lo + nbr) into `out` (new order)
+    int launch_pair(bool sample, int br_lo, int nbr, vec4 *out) {
         if (nbr <= 0) return DPD_OK;
         PairLaunch<P> pl;
         pl.sys = sys_;
@@ -1119,7 +1123,7 @@ class BatchEngine : public BatchBase {
         pl.vt = vt_;
         pl.key = key_;
         pl.cell_start = cell_start_;
-        pl.fpair = fpair_;
+        pl.fpair = out;
         pl.ev = ev_;
         pl.atab = atab_;
         pl.counter = counter_;
@@ -1191,7 +1195,7 @@ class BatchEngine : public BatchBase {
         ba.b_hi = b_hi;
         ba.sys = sys_;
         ba.bsys = bsys_;
-        ba.fpair = fpair_;
+        ba.fpair = frc_[cur_];   // the pair kernel wrote the new force buffer
         ba.pos = pos_;
         ba.key = key_;
         ba.id = id_[cur_];
@@ -1272,7 +1276,7 @@ class BatchEngine : public BatchBase {
         const int nxt = cur_ ^ 1;
         if ((rc = enqueue_sort(0, used_beads_, 0, used_cells_, cur_, nxt))) return rc;
         cur_ = nxt;
-        if ((rc = mark(1, capturing)) || (rc = launch_pair(sample, 0, used_bricks_)) ||
+        if ((rc = mark(1, capturing)) || (rc = launch_pair(sample, 0, used_bricks_, frc_[cur_])) ||
             (rc = mark(2, capturing)) ||
             (rc = enqueue_bonds(false, sample, 0, used_beads_, fuse && !sample)))
             return rc;
@@ -1403,7 +1407,7 @@ class BatchEngine : public BatchBase {
     int capmax_ = 0, xmax_ = 0, ntmax_ = 1;
     size_t smem_ = 0, smem_n_ = 0;   // pair-kernel shared memory: sampled, plain
     vec4 *pos_ = nullptr, *pos_tmp_ = nullptr, *vel_[2] = {nullptr, nullptr},
-         *frc_[2] = {nullptr, nullptr}, *vt_ = nullptr, *fpair_ = nullptr, *ev_ = nullptr;
+         *frc_[2] = {nullptr, nullptr}, *vt_ = nullptr, *ev_ = nullptr;
     uint32_t *key_ = nullptr, *key_tmp_ = nullptr, *rank_ = nullptr, *src_ = nullptr;
     int32_t *sid_ = nullptr, *id_[2] = {nullptr, nullptr}, *inv_perm_ = nullptr, *types_ = nullptr;
     LnTab *lntab_ = nullptr;

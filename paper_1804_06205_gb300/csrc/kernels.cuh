@@ -1557,7 +1557,9 @@ __device__ __forceinline__ void bond_vel_one(const BondArgs<P> &a, int t) {
         a.vel[t] = mk4<vec4, real>(v.x, v.y, v.z, (real)0);
     }
     const vec4 fn = mk4<vec4, real>(fx, fy, fz, (real)0);
-    a.frc[t] = fn;
+    // the pair kernel writes into this force buffer itself (fpair == frc):
+    // only a bead with bond terms changes it
+    if (a.frc != a.fpair || b1 > b0) a.frc[t] = fn;
     if (!FUSE) {   // (the fused update checks the positions it makes)
         if (!isfinite(fx + fy + fz + vn.x + vn.y + vn.z)) atomicOr(a.status, ST_NONFINITE);
     }

@@ -153,7 +153,7 @@ struct StepArgs {
     UpdArgs<P> upd;
     ScatterArgs<P> sc[2];
     GatherArgs<P> ga[2];
-    PairLaunch<P> pl;
+    PairLaunch<P> pl[2];             // [p].fpair: that step's force buffer
     BondArgs<P> bo[2];
     uint32_t *count, *bsum, *cell_start;
     GridBar *bar;
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1)
                 const int br = s_br;
                 __syncthreads();
                 if (br >= a.nbricks) break;
-                if (!pair_brick<P, T, false, true>(a.pl, br)) return;   // ST_TIMEOUT is set
+                if (!pair_brick<P, T, false, true>(a.pl[p], br)) return;   // ST_TIMEOUT is set
             }
         }
         if (!sync()) return;
