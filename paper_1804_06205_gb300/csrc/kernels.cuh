@@ -134,6 +134,24 @@ __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fm
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+// the hardware's approximate reciprocal square root, base-2 logarithm and
+// cosine with subnormal inputs flushed to zero: the same values as rsqrtf,
+// __log2f and __cosf for every normal input and result
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_ftz(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float cos_ftz(float x) {
+    float y;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
 
 // ln(u) for the uniforms u = n 2^-24 (n odd, n < 2^24) of the FP64 path, by the
@@ -791,9 +809,9 @@ __device__ __forceinline__ float theta_pair(uint2 x, int noise, float, const LnT
     const float u0 = u01_f32(x.x);
     if (noise) return 1.7320508075688772f * (2.0f * u0 - 1.0f);
     const float u1 = u01_f32(x.y);
-    const float q = fmaxf(-1.3862943611198906f * __log2f(u0), 0.0f);
-    const float s = q > 0.0f ? q * rsqrtf(q) : 0.0f;
-    return -s * __cosf(fmaf(6.2831853071795865f, u1, -3.1415926535897932f));
+    const float q = fmaxf(-1.3862943611198906f * lg2_ftz(u0), 0.0f);
+    const float s = q > 0.0f ? q * rsqrt_ftz(q) : 0.0f;
+    return -s * cos_ftz(fmaf(6.2831853071795865f, u1, -3.1415926535897932f));
 }
 __device__ __forceinline__ double theta_pair(uint2 x, int noise, double, const LnTab *lt) {
     return theta_of(x, noise, lt);
@@ -1131,7 +1149,7 @@ __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int br
         const float lyd = (float)(hp.y - (real)ry * hy), uyd = (float)hy - lyd;
         const float lzd = (float)(hp.z - (real)rz * hz), uzd = (float)hz - lzd;
         const float cut2 = 1.0001f;
-        // FP32: a hit is 0 < r^2 < 1 (the bead's staged copy coincides with it);
+        // FP32: a hit is 2^-126 <= r^2 < 1 (the bead's staged copy coincides with it);
         // FP64: r^2 < 1.001 in binary32 and not the bead itself, and the exact
         // test is made in the evaluation, so the hits summed are the same
         constexpr float scan_lim = P::kOffsets ? 1.0f : 1.001f;
@@ -1158,7 +1176,7 @@ __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int br
                         const float2 d = __fadd2_rn(make_float2(pj.x, pj.y), nip);
                         const float dzv = pj.z - ip.z;
                         const float r2 = fma_rn(dzv, dzv, fma_rn(d.y, d.y, mul_rn(d.x, d.x)));
-                        const float rinv = rsqrt_r(r2);
+                        const float rinv = rsqrt_ftz(r2);
                         rr1 = mul_rn(r2, rinv);
                         w = 1.0f - rr1;
                         e = __fmul2_rn(d, make_float2(rinv, rinv));
@@ -1293,15 +1311,16 @@ __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int br
                             const uint32_t ad_end = scan_u32 + 16u * (uint32_t)(qe - c0);
                             uint32_t ent = (uint32_t)(q - c0);
                             uint32_t qa = myq_u32 + 64u * (uint32_t)nh;
-                            // one candidate: its hit is 0 < r^2 < 1 (FP32: the bits of a
-                            // non-negative binary32 order like its value, so this is one
-                            // unsigned compare of the bits minus one) or binary32
-                            // r^2 < 1.001 and not the bead itself (FP64)
+                            // one candidate: its hit is 2^-126 <= r^2 < 1 (FP32: the bits
+                            // of a non-negative binary32 order like its value, so this is
+                            // one unsigned compare of the bits minus those of 2^-126; a
+                            // subnormal r^2, r < 1.1e-19, counts as coincident, like r = 0)
+                            // or binary32 r^2 < 1.001 and not the bead itself (FP64)
                             auto hit = [&](const float4 &c, uint32_t e) -> bool {
                                 const float2 d = __fadd2_rn(make_float2(c.x, c.y), nxy);
                                 const float dzv = add_rn(c.z, nzs);
                                 const float r2 = fma_rn(dzv, dzv, fma_rn(d.y, d.y, mul_rn(d.x, d.x)));
-                                return P::kOffsets ? (__float_as_uint(r2) - 1u < 0x3F7FFFFFu)
+                                return P::kOffsets ? (__float_as_uint(r2) - 0x00800000u < 0x3F000000u)
                                                    : (r2 < scan_lim && e != self);
                             };
                             auto put = [&](bool h, uint32_t e) {
