@@ -484,14 +484,43 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *total)
     return r;
 }
 
+// the SCAN_V counts of cells [b0, b0 + SCAN_V), zero past n: two 16-byte
+// loads when the run is whole and aligned
+__device__ __forceinline__ void load_counts(const uint32_t *count, int b0, int n,
+                                            uint32_t (&v)[SCAN_V]) {
+    static_assert(SCAN_V == 8, "two 16-byte loads");
+    if (b0 + SCAN_V <= n && ((uintptr_t)(count + b0) & 15u) == 0) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(count + b0);
+        const uint4 b = *reinterpret_cast<const uint4 *>(count + b0 + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < SCAN_V; ++k) v[k] = (b0 + k < n) ? count[b0 + k] : 0u;
+    }
+}
+
+// stores v[0..SCAN_V) at p[b0..) (only below n): two 16-byte stores when whole and aligned
+__device__ __forceinline__ void store_run(uint32_t *p, int b0, int n, const uint32_t (&v)[SCAN_V]) {
+    if (b0 + SCAN_V <= n && ((uintptr_t)(p + b0) & 15u) == 0) {
+        *reinterpret_cast<uint4 *>(p + b0) = make_uint4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<uint4 *>(p + b0 + 4) = make_uint4(v[4], v[5], v[6], v[7]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < SCAN_V; ++k)
+            if (b0 + k < n) p[b0 + k] = v[k];
+    }
+}
+
 static __global__ void __launch_bounds__(SCAN_T) k_scan1(const uint32_t *count, int ncell,
                                                   uint32_t *bsum) {
     griddep_wait();
     const int base = blockIdx.x * SCAN_B + threadIdx.x * SCAN_V;
+    uint32_t v[SCAN_V];
+    load_counts(count, base, ncell, v);
     uint32_t s = 0;
 #pragma unroll
-    for (int k = 0; k < SCAN_V; ++k)
-        if (base + k < ncell) s += count[base + k];
+    for (int k = 0; k < SCAN_V; ++k) s += v[k];
     __shared__ uint32_t tot;
     block_excl_scan(s, &tot);
     if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
@@ -528,20 +557,20 @@ static __global__ void __launch_bounds__(SCAN_T) k_scan3b(uint32_t *count, int n
     before = tot;
     const int b0 = blockIdx.x * SCAN_B + threadIdx.x * SCAN_V;
     uint32_t v[SCAN_V];
+    load_counts(count, b0, ncell, v);
     uint32_t sum = 0;
 #pragma unroll
-    for (int k = 0; k < SCAN_V; ++k) {
-        v[k] = (b0 + k < ncell) ? count[b0 + k] : 0u;
-        sum += v[k];
-    }
+    for (int k = 0; k < SCAN_V; ++k) sum += v[k];
     uint32_t run = block_excl_scan(sum, &tot) + before + base;
+    uint32_t st[SCAN_V];
 #pragma unroll
-    for (int k = 0; k < SCAN_V; ++k)
-        if (b0 + k < ncell) {
-            cell_start[b0 + k] = run;
-            run += v[k];
-            count[b0 + k] = 0u;
-        }
+    for (int k = 0; k < SCAN_V; ++k) {
+        st[k] = run;
+        run += v[k];
+    }
+    store_run(cell_start, b0, ncell, st);
+    const uint32_t zero[SCAN_V] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    store_run(count, b0, ncell, zero);
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == SCAN_T - 1) cell_start[ncell] = run;
 }
 
