@@ -113,7 +113,7 @@ class BatchEngine : public BatchBase {
             (rc = alloc(&vel_[1], N)) || (rc = alloc(&frc_[0], N)) || (rc = alloc(&frc_[1], N)) ||
             (rc = alloc(&vt_, N)) || (rc = alloc(&ev_, N)) ||
             (rc = alloc(&key_, N)) || (rc = alloc(&key_tmp_, N)) || (rc = alloc(&rank_, N)) ||
-            (rc = alloc(&src_, N)) || (rc = alloc(&sid_, N)) || (rc = alloc(&id_[0], N)) ||
+            (rc = alloc(&srcid_, N)) || (rc = alloc(&id_[0], N)) ||
             (rc = alloc(&id_[1], N)) || (rc = alloc(&inv_perm_, N)) || (rc = alloc(&bsys_, N)) ||
             (rc = alloc(&types_, N)) ||
             (rc = alloc(&count_, C)) || (rc = alloc(&cell_start_, C + 1)) ||
@@ -1011,16 +1011,14 @@ class BatchEngine : public BatchBase {
             sc.rank = rank_;
             sc.cell_start = cell_start_;
             sc.id_old = id_[old];
-            sc.src = src_;
-            sc.sid = sid_;
+            sc.srcid = srcid_;
             GatherArgs<P> &ga = sa.ga[p];
             ga.b_lo = 0;
             ga.b_hi = used_beads_;
             ga.sys = sys_;
             ga.bsys = bsys_;
-            ga.src = src_;
+            ga.srcid = srcid_;
             ga.cell_start = cell_start_;
-            ga.sid = sid_;
             ga.pos_tmp = pos_tmp_;
             ga.vel_old = vel_[old];
             ga.frc_old = frc_[old];
@@ -1156,17 +1154,15 @@ class BatchEngine : public BatchBase {
         sa.rank = rank_;
         sa.cell_start = cell_start_;
         sa.id_old = id_[old];
-        sa.src = src_;
-        sa.sid = sid_;
+        sa.srcid = srcid_;
         DPD_CU(launch_pdl(k_scatter<P>, blocks(b_hi - b_lo), 256, 0, stream_, sa));
         GatherArgs<P> ga;
         ga.b_lo = b_lo;
         ga.b_hi = b_hi;
         ga.sys = sys_;
         ga.bsys = bsys_;
-        ga.src = src_;
+        ga.srcid = srcid_;
         ga.cell_start = cell_start_;
-        ga.sid = sid_;
         ga.pos_tmp = pos_tmp_;
         ga.vel_old = vel_[old];
         ga.frc_old = frc_[old];
@@ -1408,8 +1404,9 @@ class BatchEngine : public BatchBase {
     size_t smem_ = 0, smem_n_ = 0;   // pair-kernel shared memory: sampled, plain
     vec4 *pos_ = nullptr, *pos_tmp_ = nullptr, *vel_[2] = {nullptr, nullptr},
          *frc_[2] = {nullptr, nullptr}, *vt_ = nullptr, *ev_ = nullptr;
-    uint32_t *key_ = nullptr, *key_tmp_ = nullptr, *rank_ = nullptr, *src_ = nullptr;
-    int32_t *sid_ = nullptr, *id_[2] = {nullptr, nullptr}, *inv_perm_ = nullptr, *types_ = nullptr;
+    uint32_t *key_ = nullptr, *key_tmp_ = nullptr, *rank_ = nullptr;
+    uint2 *srcid_ = nullptr;
+    int32_t *id_[2] = {nullptr, nullptr}, *inv_perm_ = nullptr, *types_ = nullptr;
     LnTab *lntab_ = nullptr;
     int *bsys_ = nullptr, *brick_sys_ = nullptr, *old_bead0_ = nullptr;
     uint32_t *count_ = nullptr, *cell_start_ = nullptr, *bsum_ = nullptr;

@@ -583,16 +583,14 @@ struct ScatterArgs {
     int sys1;                        // the only system of a batch of one, else -1
     const uint32_t *key_tmp, *rank, *cell_start;
     const int32_t *id_old;
-    uint32_t *src;
-    int32_t *sid;
+    uint2 *srcid;                    // per arrival slot: (source slot, id)
 };
 
 template <class P>
 __device__ __forceinline__ void scatter_one(const ScatterArgs<P> &a, int t) {
     const int s = bead_sys(a, t);
     const uint32_t slot = a.cell_start[a.sys[s].cell0 + a.key_tmp[t]] + a.rank[t];
-    a.src[slot] = (uint32_t)t;
-    a.sid[slot] = a.id_old[t];
+    a.srcid[slot] = make_uint2((uint32_t)t, (uint32_t)a.id_old[t]);
 }
 
 template <class P>
@@ -609,8 +607,8 @@ struct GatherArgs {
     const SysDesc<P> *sys;
     const int *bsys;
     int sys1;                        // the only system of a batch of one, else -1
-    const uint32_t *src, *cell_start;
-    const int32_t *sid;
+    const uint2 *srcid;              // per arrival slot: (source slot, id)
+    const uint32_t *cell_start;
     const vec4 *pos_tmp, *vel_old, *frc_old;
     const uint32_t *key_tmp;
     vec4 *pos, *vel, *frc, *vt;
@@ -628,13 +626,14 @@ struct GatherArgs {
 template <class P, bool MOVE_VF>
 __device__ __forceinline__ void gather_one(const GatherArgs<P> &a, int t) {
     const SysDesc<P> &D = a.sys[bead_sys(a, t)];
-    const uint32_t s = a.src[t];
-    const int32_t i = a.sid[t];
+    const uint2 si = a.srcid[t];
+    const uint32_t s = si.x;
+    const int32_t i = (int32_t)si.y;
     const uint32_t k = a.key_tmp[s];
     const uint32_t c = (uint32_t)D.cell0 + k;
     const int b = (int)a.cell_start[c], e = (int)a.cell_start[c + 1];
     int u = b;
-    for (int q = b; q < e; ++q) u += a.sid[q] < i;
+    for (int q = b; q < e; ++q) u += (int32_t)a.srcid[q].y < i;
     const typename P::vec4 v = a.vel_old[s], f = a.frc_old[s];
     const typename P::real lam_dt = D.lam_dt;
     a.pos[u] = a.pos_tmp[s];
