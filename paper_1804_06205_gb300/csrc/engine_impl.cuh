@@ -526,16 +526,29 @@ class BatchEngine : public BatchBase {
         int rc = ensure_io((size_t)h.n);   // 72 B per bead: holds either record
         if (rc) return rc;
         k_inv_perm<<<blocks(h.n), 256, 0, stream_>>>(h.bead0, h.n, id_[cur_], inv_perm_);
-        k_ckpt_out<P><<<blocks(h.n), 256, 0, stream_>>>(s, sys_, pos_, key_, vel_[cur_],
-                                                          frc_[cur_], inv_perm_,
-                                                          reinterpret_cast<Rec *>(io_));
-        launches_ += 2;
+        ++launches_;
         DPD_CU(cudaGetLastError());
         CkptHeader hd;
         fill_header(h, hd);
         std::memcpy(buf, &hd, sizeof(hd));
-        DPD_CU(cudaMemcpyAsync(static_cast<char *>(buf) + sizeof(hd), io_,
-                               (size_t)h.n * sizeof(Rec), cudaMemcpyDeviceToHost, stream_));
+        // records in chunks of ids, each copied to the host on the copy stream
+        // while the next one is gathered
+        Rec *dst = reinterpret_cast<Rec *>(static_cast<char *>(buf) + sizeof(hd));
+        Rec *rio = reinterpret_cast<Rec *>(io_);
+        const int nch = io_chunks(h.n);
+        for (int c = 0; c < nch; ++c) {
+            const int i0 = (int)((int64_t)h.n * c / nch), i1 = (int)((int64_t)h.n * (c + 1) / nch);
+            k_ckpt_out<P><<<blocks(i1 - i0), 256, 0, stream_>>>(s, i0, i1, sys_, pos_, key_,
+                                                                 vel_[cur_], frc_[cur_],
+                                                                 inv_perm_, rio);
+            ++launches_;
+            DPD_CU(cudaGetLastError());
+            DPD_CU(cudaEventRecord(xev_[c], stream_));
+            DPD_CU(cudaStreamWaitEvent(xfer_, xev_[c], 0));
+            DPD_CU(cudaMemcpyAsync(dst + i0, rio + i0, (size_t)(i1 - i0) * sizeof(Rec),
+                                   cudaMemcpyDeviceToHost, xfer_));
+        }
+        DPD_CU(cudaStreamSynchronize(xfer_));
         DPD_CU(cudaStreamSynchronize(stream_));
         return check_status();
     }
@@ -575,13 +588,24 @@ class BatchEngine : public BatchBase {
         ia.count = count_;
         ia.id = id_[old];
         ia.status = status_;
-        ia.i0 = 0;
-        ia.i1 = h.n;
-        DPD_CU(cudaMemcpyAsync(io_, rec, (size_t)h.n * sizeof(Rec), cudaMemcpyHostToDevice,
-                               stream_));
-        k_ckpt_in<P><<<blocks(h.n), 256, 0, stream_>>>(ia, reinterpret_cast<const Rec *>(io_));
-        ++launches_;
-        DPD_CU(cudaGetLastError());
+        // records copied in chunks on the copy stream, each restored as soon as
+        // it has landed (the staging buffer is free once earlier work is done)
+        Rec *rio = reinterpret_cast<Rec *>(io_);
+        DPD_CU(cudaEventRecord(xev_[IO_MAXCH], stream_));
+        DPD_CU(cudaStreamWaitEvent(xfer_, xev_[IO_MAXCH], 0));
+        const int nch = io_chunks(h.n);
+        for (int c = 0; c < nch; ++c) {
+            const int i0 = (int)((int64_t)h.n * c / nch), i1 = (int)((int64_t)h.n * (c + 1) / nch);
+            DPD_CU(cudaMemcpyAsync(rio + i0, rec + i0, (size_t)(i1 - i0) * sizeof(Rec),
+                                   cudaMemcpyHostToDevice, xfer_));
+            DPD_CU(cudaEventRecord(xev_[c], xfer_));
+            DPD_CU(cudaStreamWaitEvent(stream_, xev_[c], 0));
+            ia.i0 = i0;
+            ia.i1 = i1;
+            k_ckpt_in<P><<<blocks(i1 - i0), 256, 0, stream_>>>(ia, rio);
+            ++launches_;
+            DPD_CU(cudaGetLastError());
+        }
         long long sv = (long long)got.step;
         DPD_CU(cudaMemcpyAsync(counter_ + s, &sv, sizeof(long long), cudaMemcpyHostToDevice,
                                stream_));

@@ -1817,15 +1817,15 @@ struct CkptRec<PF64> {
 };
 
 template <class P>
-__global__ void __launch_bounds__(256) k_ckpt_out(int s, const SysDesc<P> *sys,
+__global__ void __launch_bounds__(256) k_ckpt_out(int s, int i0, int i1, const SysDesc<P> *sys,
                                                   const typename P::vec4 *pos, const uint32_t *key,
                                                   const typename P::vec4 *vel,
                                                   const typename P::vec4 *frc,
                                                   const int32_t *inv_perm,
                                                   typename CkptRec<P>::type *out) {
     const SysDesc<P> &D = sys[s];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= D.n) return;
+    const int i = i0 + blockIdx.x * blockDim.x + threadIdx.x;   // ids [i0, i1)
+    if (i >= i1) return;
     const int t = inv_perm[D.bead0 + i];
     const typename P::vec4 p = pos[t], v = vel[t], f = frc[t];
     typename CkptRec<P>::type r;
