@@ -39,6 +39,30 @@ def _straight(D, w, prec, nsteps):
 
 
 @pytest.mark.parametrize("prec", [FP32, FP64])
+def test_resume_from_records_copied_in_chunks(D, prec):
+    """A system of 600k beads: its records cross the host link in several
+    chunks of ids, each restored (or read out) while the next one moves, and
+    the resumed run still equals the uninterrupted one bit for bit."""
+    w = W.fluid(58.5, ntypes=2, a_same=25.0, a_cross=30.0, seed=63)
+    assert w.n >= 2 * (1 << 18)
+    n = 2
+    ref = _straight(D, w, prec, n)
+    g = D.System.from_workload(w, precision=prec)
+    g.set_state(w.pos, w.vel, 0)
+    g.step(n)
+    ck = g.get_checkpoint()
+    g.close()
+    h = D.System.from_workload(w, precision=prec)
+    h.set_checkpoint(ck)
+    assert h.get_checkpoint() == ck
+    h.step(n)
+    out = h.get_state()
+    h.close()
+    for a, b in zip(ref[:3], out[:3]):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
 def test_resume_alone_is_bitwise(D, prec):
     w = _workload()
     n = 12
