@@ -663,7 +663,8 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs<P> a) {
 //
 // A block owns a brick of X x BY x BZ home cells (BY, BZ <= 2).  It stages the
 // (BY+2)(BZ+2) neighbouring x-row runs (X+2 cells each, periodic) into shared
-// memory -- positions in the brick's frame (cell index relative to the
+// memory with bulk copies, issued as soon as the runs' source ranges are
+// known -- positions in the brick's frame (cell index relative to the
 // brick, times h, plus the offset; FP64: the absolute position moved by the
 // run's periodic image) and v~.  A home bead's 27 neighbour cells are 9 rows
 // of 3 consecutive staged cells; a row, or its first or last cell, is skipped
@@ -674,8 +675,9 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs<P> a) {
 //            own queue, at most PAIR_HMAX per pass (binary32 on both paths;
 //            FP64 queues every pair with binary32 r^2 < 1.001 and the
 //            evaluation applies the exact FP64 test);
-//   evaluate every lane evaluates its own queue in order and adds the pair
-//            forces to its bead's sums in registers.  FP64, when a block
+//   evaluate every lane evaluates its own queue in order (FP32: two entries
+//            per iteration, added in queue order) and adds the pair forces
+//            to its bead's sums in registers.  FP64, when a block
 //            needs one chunk and one pass: thread t evaluates the queue of
 //            the block's bead of rank t by hit count, so that a warp's
 //            queues have similar lengths (idle lanes still hold the FP64
@@ -738,7 +740,7 @@ struct PairSmem {
         using vec4 = typename P::vec4;
         size_t b = 2 * (size_t)cap * sizeof(vec4);                 // staged positions, v~
         if (!P::kOffsets) b += (size_t)cap * sizeof(float4);      // FP64: their binary32 copies
-        b += 2 * PAIR_NR * (size_t)(X + 3) * sizeof(int);          // staged / source cell starts
+        b += 2 * PAIR_NR * (size_t)(X + 3) * sizeof(int);          // staged cell starts; FP64 ranks
         b += PAIR_NR * 3 * PAIR_PC * sizeof(int) + 4 * 4 * sizeof(int);   // runs, home rows
         b += PAIR_NR * sizeof(int);                                // row keys
         b = align16(b);
@@ -893,8 +895,8 @@ __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int br
     // FP64 path: binary32 copies of the staged frame positions, for the scan
     float4 *s_p32 = reinterpret_cast<float4 *>(s_vt + cap);
     int *s_cs = reinterpret_cast<int *>(s_p32 + (P::kOffsets ? 0 : cap));
-    int *s_src = s_cs + PAIR_NR * (la.Xmax + 3);
-    int *s_pc = s_src + PAIR_NR * (la.Xmax + 3);
+    int *s_src = s_cs + PAIR_NR * (la.Xmax + 3);   // FP64: the balanced evaluation's ranks
+    int *s_pc = s_src + PAIR_NR * (la.Xmax + 3);   // per source run: source slot, staged slot, length
     int *s_hr = s_pc + PAIR_NR * 3 * PAIR_PC;        // home rows: staged row, first, count, global
     int *s_rkey = s_hr + 16;                         // per staged row: key of its cell x = 0
     size_t off = PairSmem<P>::align16((size_t)((unsigned char *)(s_rkey + PAIR_NR) - smem));
