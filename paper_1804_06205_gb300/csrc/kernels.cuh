@@ -116,8 +116,9 @@ __device__ __forceinline__ uint2 philox_xy(uint32_t c0, uint32_t c1, uint32_t c2
 // Uniform (2*(x>>9)+1) * 2^-24 in (0, 1), exact in binary32.
 __device__ __forceinline__ float u01_f32(uint32_t x) {
     // ((x >> 8) | 1) * 2^-24 built without an int->float conversion: 1 + (x>>9)
-    // 2^-23 by its bits, minus 1 and plus 2^-24, both exact
-    return __fadd_rn(__fsub_rn(__uint_as_float(0x3F800000u | (x >> 9)), 1.0f), 0x1p-24f);
+    // 2^-23 by its bits, minus 1 - 2^-24 (exact: the operands are within a
+    // factor 2 of each other, and the result (2 (x>>9) + 1) 2^-24 has 24 bits)
+    return __fsub_rn(__uint_as_float(0x3F800000u | (x >> 9)), 0x1.fffffep-1f);
 }
 __device__ __forceinline__ double u01_f64(uint32_t x) {
     return (double)((x >> 8) | 1u) * 0x1p-24;
