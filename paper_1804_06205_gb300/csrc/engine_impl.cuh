@@ -66,6 +66,7 @@ class BatchEngine : public BatchBase {
         int64_t step = 0;
         int red0 = 0, nred = 0, rsys_index = 0;   // reduction chunks, entry in rsys
         bool obs_fresh = false;   // obs_ holds the observables of the current state
+        bool unsorted = false;    // restored in bead-id order; no cell order or cell starts yet
     };
 
     struct GraphSlot {
@@ -310,6 +311,7 @@ class BatchEngine : public BatchBase {
             (rc = launch_pair(false, h.brick0, h.nbrick, frc_[cur_])) ||
             (rc = enqueue_bonds(true, false, h.bead0, h.bead0 + h.n)))
             return rc;
+        h.unsorted = false;
         h.obs_fresh = false;
         DPD_CU(cudaStreamSynchronize(stream_));
         int st = 0;
@@ -341,6 +343,7 @@ class BatchEngine : public BatchBase {
             for (int s : order_) {
                 hs_[s].step += nsteps;
                 hs_[s].obs_fresh = false;
+                hs_[s].unsorted = false;
             }
             return DPD_OK;
         }
@@ -363,7 +366,10 @@ class BatchEngine : public BatchBase {
             for (int s : order_) hs_[s].step += 1;
         }
         if (nsteps > 0)
-            for (int s : order_) hs_[s].obs_fresh = sampled;
+            for (int s : order_) {
+                hs_[s].obs_fresh = sampled;
+                hs_[s].unsorted = false;
+            }
         return DPD_OK;
     }
 
@@ -412,7 +418,7 @@ class BatchEngine : public BatchBase {
         if (!h.has_state) return DPD_ENOSTATE;
         if (!h.obs_fresh) {   // the sampled pair sums and the bond sums of this state
             int rc = check_status();
-            if (rc) return rc;
+            if (rc || (rc = ensure_sorted(s))) return rc;
             // the forces go to the other buffer, free between steps; only the
             // sampled sums are kept
             if ((rc = launch_pair(true, h.brick0, h.nbrick, frc_[cur_ ^ 1])) ||
@@ -454,6 +460,8 @@ class BatchEngine : public BatchBase {
         SysHost &h = hs_[s];
         if (!h.has_state) return DPD_ENOSTATE;
         if (!(rmax > 0) || nbins <= 0 || nbins > 4096 || !counts) return DPD_EINVAL;
+        int rc0 = ensure_sorted(s);
+        if (rc0) return rc0;
         int K[3];
         for (int k = 0; k < 3; ++k) {
             K[k] = (int)std::ceil(rmax * h.cfg.inv_h[k]);
@@ -483,7 +491,7 @@ class BatchEngine : public BatchBase {
         if (!h.has_state) return DPD_ENOSTATE;
         const size_t n = (size_t)h.n, C = (size_t)h.ncell;
         int rc = ensure_io(n);
-        if (rc) return rc;
+        if (rc || (rc = ensure_sorted(s))) return rc;
         uint32_t *dk = reinterpret_cast<uint32_t *>(io_);
         int64_t *dord = reinterpret_cast<int64_t *>(io_ + 3 * n);
         k_cells_out<P><<<blocks(h.n), 256, 0, stream_>>>(s, sys_, key_, id_[cur_], dk, dord);
@@ -574,19 +582,22 @@ class BatchEngine : public BatchBase {
         }
         const Rec *rec = reinterpret_cast<const Rec *>(static_cast<const char *>(buf) + sizeof(got));
         if ((rc = ensure_io((size_t)h.n))) return rc;
-        const int old = cur_ ^ 1;
+        // the records go straight into the state arrays, in bead-id order: the
+        // next step's position update takes the beads in any order and its cell
+        // division puts them in the canonical order, so no sort is spent here;
+        // calls that need the cell order first sort (ensure_sorted)
         InitArgs<P> ia;
         ia.s = s;
         ia.sys = sys_;
         ia.pos_in = ia.vel_in = nullptr;
         ia.types = types_ + h.bead0;
-        ia.pos_tmp = pos_tmp_;
-        ia.vel = vel_[old];
-        ia.frc = frc_[old];
-        ia.key_tmp = key_tmp_;
-        ia.rank = rank_;
-        ia.count = count_;
-        ia.id = id_[old];
+        ia.pos_tmp = pos_;
+        ia.vel = vel_[cur_];
+        ia.frc = frc_[cur_];
+        ia.key_tmp = key_;
+        ia.rank = nullptr;
+        ia.count = nullptr;
+        ia.id = id_[cur_];
         ia.status = status_;
         // records copied in chunks on the copy stream, each restored as soon as
         // it has landed (the staging buffer is free once earlier work is done)
@@ -609,9 +620,7 @@ class BatchEngine : public BatchBase {
         long long sv = (long long)got.step;
         DPD_CU(cudaMemcpyAsync(counter_ + s, &sv, sizeof(long long), cudaMemcpyHostToDevice,
                                stream_));
-        if ((rc = enqueue_sort(h.bead0, h.bead0 + h.n, h.cell0, h.cell0 + h.ncell, old, cur_,
-                               true)))
-            return rc;
+        h.unsorted = true;
         h.obs_fresh = false;
         DPD_CU(cudaStreamSynchronize(stream_));
         int st = 0;
@@ -626,6 +635,24 @@ class BatchEngine : public BatchBase {
         h.has_state = true;
         h.step = got.step;
         return check_status();
+    }
+
+    // A system restored in bead-id order gets its cell order and cell starts
+    // (the cell division of set_state, from the state arrays) before a call
+    // that needs them; a step does this by itself.
+    int ensure_sorted(int s) {
+        SysHost &h = hs_[s];
+        if (!h.unsorted) return DPD_OK;
+        const int old = cur_ ^ 1;
+        k_resort_prep<P><<<blocks(h.n), 256, 0, stream_>>>(
+            s, sys_, pos_, key_, vel_[cur_], frc_[cur_], id_[cur_], pos_tmp_, key_tmp_, rank_,
+            count_, vel_[old], frc_[old], id_[old]);
+        ++launches_;
+        DPD_CU(cudaGetLastError());
+        int rc = enqueue_sort(h.bead0, h.bead0 + h.n, h.cell0, h.cell0 + h.ncell, old, cur_, true);
+        if (rc) return rc;
+        h.unsorted = false;
+        return DPD_OK;
     }
 
     int sync() override {

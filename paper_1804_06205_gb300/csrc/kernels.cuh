@@ -1873,10 +1873,37 @@ __global__ void __launch_bounds__(256) k_ckpt_in(InitArgs<P> a,
     if (!fin) atomicOr(a.status, ST_BADINPUT);
     a.pos_tmp[t] = out;
     a.key_tmp[t] = key;
-    a.rank[t] = atomicAdd(&a.count[D.cell0 + key], 1u);
+    if (a.count) a.rank[t] = atomicAdd(&a.count[D.cell0 + key], 1u);   // null: no sort follows
     a.vel[t] = mk4<typename P::vec4, real>(r.v[0], r.v[1], r.v[2], (real)0);
     a.frc[t] = mk4<typename P::vec4, real>(r.f[0], r.f[1], r.f[2], (real)0);
     a.id[t] = i;
+}
+
+// The state of beads [bead0, bead0 + n) of system s, held in any order, as the
+// input of a cell division: position and key into the sort's work arrays with
+// an arrival rank, v, f and id into the other ping-pong buffers.
+template <class P>
+__global__ void __launch_bounds__(256) k_resort_prep(int s, const SysDesc<P> *sys,
+                                                     const typename P::vec4 *pos,
+                                                     const uint32_t *key,
+                                                     const typename P::vec4 *vel,
+                                                     const typename P::vec4 *frc,
+                                                     const int32_t *id,
+                                                     typename P::vec4 *pos_tmp, uint32_t *key_tmp,
+                                                     uint32_t *rank, uint32_t *count,
+                                                     typename P::vec4 *vel_old,
+                                                     typename P::vec4 *frc_old, int32_t *id_old) {
+    const SysDesc<P> &D = sys[s];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= D.n) return;
+    const int t = D.bead0 + k;
+    const uint32_t c = key[t];
+    pos_tmp[t] = pos[t];
+    key_tmp[t] = c;
+    rank[t] = atomicAdd(&count[D.cell0 + c], 1u);
+    vel_old[t] = vel[t];
+    frc_old[t] = frc[t];
+    id_old[t] = id[t];
 }
 
 template <class P>
