@@ -155,26 +155,29 @@ __device__ __forceinline__ float cos_ftz(float x) {
 }
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
 
-// ln(u) for the uniforms u = n 2^-24 (n odd, n < 2^24) of the FP64 path, by the
-// table-driven method of P. T. P. Tang (ACM TOMS 16, 1990): with e = floor(log2 n)
-// and j the next seven bits of n, n = 2^e (1 + j/128) + rest, and
+// -2 ln(u) for the uniforms u = n 2^-24 (n odd, n < 2^24) of the FP64 path, by
+// the table-driven method of P. T. P. Tang (ACM TOMS 16, 1990): with
+// e = floor(log2 n) and j the next seven bits of n, n = 2^e (1 + j/128) + rest, and
 //   ln u = (e - 24) ln 2 + ln(1 + j/128) + log1p(r),  r = rest 2^-e / (1 + j/128),
 // |r| < 2^-7, log1p(r) by its Taylor series to r^7 / 7 (the next term is below
 // 2e-18).  The reduction is integer arithmetic; the tables are filled with the
-// library's log.  Ten FP64 operations instead of a general log.
+// library's log.  The tables and coefficients carry the factor -2 of Box-Muller:
+// scaling by a power of two commutes with rounding, so every step, and the
+// result, is exactly -2 times that of the same evaluation of ln u.  Ten FP64
+// operations instead of a general log.
 struct LnTab {
-    double2 c[128];   // ln(1 + j/128), 1 / (1 + j/128)
-    double e[24];     // (e - 24) ln 2
+    double2 c[128];   // -2 ln(1 + j/128), 1 / (1 + j/128)
+    double e[24];     // -2 (e - 24) ln 2
 };
 static __global__ void k_ln_tab(LnTab *t) {
     const int j = threadIdx.x;
     if (j < 128) {
         const double c = 1.0 + j / 128.0;
-        t->c[j] = make_double2(log(c), 1.0 / c);
+        t->c[j] = make_double2(-2.0 * log(c), 1.0 / c);
     }
-    if (j < 24) t->e[j] = (double)(j - 24) * log(2.0);
+    if (j < 24) t->e[j] = -2.0 * ((double)(j - 24) * log(2.0));
 }
-__device__ __forceinline__ double ln_u24(uint32_t n, const LnTab *t) {
+__device__ __forceinline__ double m2ln_u24(uint32_t n, const LnTab *t) {
     const int e = 31 - __clz(n);
     int j;
     uint32_t rest;
@@ -189,12 +192,12 @@ __device__ __forceinline__ double ln_u24(uint32_t n, const LnTab *t) {
     // (1 + j/128)^-1 2^-e through the exponent field: exact, no underflow for e < 24
     const double inv = __longlong_as_double(__double_as_longlong(cj.y) - ((long long)e << 52));
     const double r = (double)rest * inv;
-    double p = fma(r, 1.0 / 7.0, -1.0 / 6.0);
-    p = fma(r, p, 1.0 / 5.0);
-    p = fma(r, p, -1.0 / 4.0);
-    p = fma(r, p, 1.0 / 3.0);
-    p = fma(r, p, -1.0 / 2.0);
-    p = fma(r, p, 1.0);
+    double p = fma(r, -2.0 / 7.0, 2.0 / 6.0);
+    p = fma(r, p, -2.0 / 5.0);
+    p = fma(r, p, 2.0 / 4.0);
+    p = fma(r, p, -2.0 / 3.0);
+    p = fma(r, p, 2.0 / 2.0);
+    p = fma(r, p, -2.0);
     return t->e[e] + fma(r, p, cj.x);
 }
 // cos(2 pi v) for the uniforms v = a 2^-24 (a odd, a < 2^24) of the FP64 path.
@@ -202,14 +205,13 @@ __device__ __forceinline__ double ln_u24(uint32_t n, const LnTab *t) {
 // arithmetic: with b the remaining 22 bits, 2 pi v = q pi/2 + (pi/2) b 2^-22,
 // and cos(q pi/2 + phi) = +-cos(psi) with psi = phi (q even) or pi/2 - phi (q
 // odd), psi = (pi/2) c 2^-22 in [0, pi/2].  cos(psi) is its Taylor series to
-// psi^22 / 22! (the next term is below 1e-19).
+// psi^20 / 20! (the next term is below 2e-17 in absolute value).
 __device__ __forceinline__ double cos_u24(uint32_t a) {
     const uint32_t q = a >> 22, b = a & 0x3FFFFFu;
     const uint32_t c = (q & 1u) ? 0x400000u - b : b;
     const double psi = (double)c * (3.141592653589793 / 8388608.0);   // c pi 2^-23, pi/2^23 exact
     const double s = psi * psi;
-    double p = -1.0 / 1124000727777607680000.0;
-    p = fma(s, p, 1.0 / 2432902008176640000.0);
+    double p = 1.0 / 2432902008176640000.0;
     p = fma(s, p, -1.0 / 6402373705728000.0);
     p = fma(s, p, 1.0 / 20922789888000.0);
     p = fma(s, p, -1.0 / 87178291200.0);
@@ -226,7 +228,7 @@ __device__ __forceinline__ double cos_u24(uint32_t a) {
 // theta from Box-Muller on outputs 0 and 1 (noise 0) or sqrt(3)(2u-1) (noise 1).
 __device__ __forceinline__ double theta_of(uint2 x, int noise, const LnTab *lt) {
     if (noise) return 1.7320508075688772 * (2.0 * u01_f64(x.x) - 1.0);
-    return sqrt(-2.0 * ln_u24((x.x >> 8) | 1u, lt)) * cos_u24((x.y >> 8) | 1u);
+    return sqrt(m2ln_u24((x.x >> 8) | 1u, lt)) * cos_u24((x.y >> 8) | 1u);
 }
 
 // --------------------------------------------------------------------------
@@ -660,7 +662,7 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs<P> a) {
 
 // --------------------------------------------------------------------------
 // a4-a5: pair forces, 27-cell full shell: every bead's force is summed in a
-// fixed order by one thread, with no force atomics.
+// fixed order by one thread, with no floating-point atomics.
 //
 // A block owns a brick of X x BY x BZ home cells (BY, BZ <= 2).  It stages the
 // (BY+2)(BZ+2) neighbouring x-row runs (X+2 cells each, periodic) into shared
@@ -682,7 +684,10 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs<P> a) {
 //            needs one chunk and one pass: thread t evaluates the queue of
 //            the block's bead of rank t by hit count, so that a warp's
 //            queues have similar lengths (idle lanes still hold the FP64
-//            pipe).
+//            pipe); when that pass holds every home bead, each pair of two
+//            home beads is evaluated by one of them, which hands the other
+//            its share as exact fixed point (integer atomics, so the sum
+//            does not depend on their order).
 // Passes repeat until all 27 cells are done; oversized neighbourhoods are
 // staged in chunks.  Each bead's force is summed in a fixed order, so runs
 // are deterministic; another brick shape changes only the order of the
@@ -731,6 +736,7 @@ constexpr int PAIR_HMAX = 32;          // hits per lane per pass
 constexpr int PAIR_NR = 16;            // staged rows, (2+2) x (2+2)
 static_assert(PAIR_HMAX >= 1 && PAIR_HMAX <= 64, "hit queue length");
 constexpr int PAIR_THREADS_PER_SM = 896; // FP32 register budget: 28 warps per SM
+constexpr int PAIR64_THREADS_PER_SM = 384; // FP64 register budget: 12 warps per SM
 constexpr int PAIR_PC = 3;             // ints per staged run: source, slot, length
 
 template <class P>
@@ -749,6 +755,11 @@ struct PairSmem {
         b = align16(b);
         const size_t nw = (size_t)T / 32;
         b += nw * PAIR_HMAX * 32 * sizeof(uint16_t);               // hit queues
+        if (!P::kOffsets) {   // FP64 pairs of two home beads: partner shares, home index
+            b = align16(b);
+            b += 3 * (size_t)T * sizeof(unsigned long long);
+            b += (size_t)cap * sizeof(int16_t);
+        }
         (void)sample;
         return b;
     }
@@ -905,6 +916,12 @@ __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int br
     real *s_rsh = s_a + la.ntmax * la.ntmax;         // per staged row: y, z frame shift
     off = PairSmem<P>::align16((size_t)((unsigned char *)(s_rsh + 2 * PAIR_NR) - smem));
     uint16_t *s_q = reinterpret_cast<uint16_t *>(smem + off);   // per-lane hit queues
+    // FP64: each home bead's share of the pairs that a home partner evaluated
+    // (x, y, z; two's-complement fixed point in units of 2^-41), and the home
+    // index of each staged slot (-1: not a home bead)
+    off = PairSmem<P>::align16(off + (size_t)(T / 32) * PAIR_HMAX * 32 * sizeof(uint16_t));
+    unsigned long long *s_acc = reinterpret_cast<unsigned long long *>(smem + off);
+    int16_t *s_hidx = reinterpret_cast<int16_t *>(s_acc + 3 * T);
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     __shared__ __align__(8) uint64_t s_mbar;   // completion of the staging copies
@@ -1187,6 +1204,9 @@ __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int br
         const float4 *s_scan = P::kOffsets ? reinterpret_cast<const float4 *>(s_pos) : s_p32;
         const int self_abs = active ? s_cs[sr_home * W + 1] + (hb - s_hr[4 * hr + 1]) : -1;
 
+        // FP64, one pass over every home bead: each pair of two home beads is
+        // evaluated by one of them (once), which sets wide if a share did not fit
+        bool once = false, wide = false;
         // the queue qb[m * 32 + col], m < n, of the bead at ip (v~ iv): each
         // lane takes its entries in scan order and adds them to the sums
         auto evaluate = [&](const uint16_t *qb, int col, int n, const vec4 &ip, const vec4 &iv,
@@ -1262,23 +1282,50 @@ __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int br
                             const real rinv = rsqrt_r(r2);
                             const real rr1 = mul_rn(r2, rinv);
                             const real w = (real)1 - rr1;
-                            const real ex = mul_rn(dx, rinv), ey = mul_rn(dyv, rinv), ez = mul_rn(dzv, rinv);
-                            const real evel = fma_rn(ez, iv.z - vj.z,
-                                                     fma_rn(ey, iv.y - vj.y, mul_rn(ex, iv.x - vj.x)));
+                            // e.v_ij = (d.v_ij) / r; F = w S e with S = a_ij - gamma w e.v_ij
+                            // + sigma theta / sqrt(dt), added as (w / r) S d, w / r = 1/r - 1
+                            const real dvx = iv.x - vj.x, dvy = iv.y - vj.y, dvz = iv.z - vj.z;
+                            const real evel = mul_rn(fma_rn(dzv, dvz, fma_rn(dyv, dvy, mul_rn(dx, dvx))), rinv);
                             const real aij = s_a[P::unpack_int(ip.w) * nt + P::unpack_int(pj.w)];
                             const int32_t idi = P::unpack_int(iv.w), idj = P::unpack_int(vj.w);
                             const uint32_t lo = (uint32_t)min(idi, idj), hi = (uint32_t)max(idi, idj);
                             const uint2 rnd = philox_rk(lo, hi, s_lo, s_hi, rkl);
                             const real th = theta_pair(rnd, a.noise, (real)0, la.lntab);
-                            const real fc = mul_rn(aij, w);
-                            const real gw2 = mul_rn(mul_rn(a.gamma, w), w);
-                            const real mag = fma_rn(mul_rn(a.sig_sqdt, w), th, fma_rn(-gw2, evel, fc));
-                            sx = add_rn(sx, mul_rn(mag, ex));
-                            sy = add_rn(sy, mul_rn(mag, ey));
-                            sz = add_rn(sz, mul_rn(mag, ez));
+                            const real S = fma_rn(a.sig_sqdt, th, fma_rn(-mul_rn(a.gamma, w), evel, aij));
+                            const real magr = mul_rn(rinv - (real)1, S);
+                            sx = fma_rn(magr, dx, sx);
+                            sy = fma_rn(magr, dyv, sy);
+                            sz = fma_rn(magr, dzv, sz);
+                            bool both = false;   // this pair's terms count for both beads
+                            if (once) {
+                                const int hj = s_hidx[jl];
+                                if (hj >= 0) {
+                                    // a home partner: it receives -F in fixed point (units of
+                                    // 2^-41, exact sums in any order).  With |F_c| <= |magr| r
+                                    // < 2^9 (from the exponents of magr and r) a share is
+                                    // below 2^50, so one fused multiply-add with 1.5 * 2^52
+                                    // rounds it to an integer held in the low bits, and the
+                                    // sum of at most PAIR_HMAX shares stays below 2^55
+                                    both = true;
+                                    const int em = (__double2hiint(magr) >> 20) & 0x7ff;
+                                    const int er = (__double2hiint(rr1) >> 20) & 0x7ff;
+                                    if (em + er <= 2 * 1023 + 7) {
+                                        unsigned long long *acc = s_acc + 3 * hj;
+                                        const real ms = mul_rn(magr, 0x1p41);
+                                        const long long m52 = 0x4338000000000000ll;   // 1.5 * 2^52
+                                        atomicAdd(acc, (unsigned long long)(m52 - __double_as_longlong(fma_rn(ms, dx, 0x1.8p52))));
+                                        atomicAdd(acc + 1, (unsigned long long)(m52 - __double_as_longlong(fma_rn(ms, dyv, 0x1.8p52))));
+                                        atomicAdd(acc + 2, (unsigned long long)(m52 - __double_as_longlong(fma_rn(ms, dzv, 0x1.8p52))));
+                                    } else {
+                                        wide = true;   // a large or non-finite force
+                                    }
+                                }
+                            }
                             if (SAMPLE) {
-                                sw += rr1 * fc;
-                                se += (real)0.5 * fc * w;
+                                const real fc = mul_rn(aij, w);
+                                const real tw = rr1 * fc, te = (real)0.5 * fc * w;
+                                sw += both ? tw + tw : tw;
+                                se += both ? te + te : te;
                             }
                         }
                     }
@@ -1392,11 +1439,42 @@ __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int br
                 // of rank t by hit count (most first), so that a warp's queues have
                 // similar lengths: lanes left idle by short queues still occupy the
                 // FP64 pipe.  Each bead's terms are added in scan order as before.
-                if (tid <= PAIR_HMAX) s_pc[tid] = 0;     // histogram of hit counts
-                int nh = 0;
-                scan(nh);
-                __syncwarp();
-                if (!__syncthreads_or(more)) {
+                // When the pass holds every home bead, each pair of two home beads
+                // is evaluated once, by one of them, and the other one's queue drops
+                // it: the FP64 pipe then computes about a third fewer pair terms.
+                once = H <= T;
+                for (;;) {
+                    if (tid <= PAIR_HMAX) s_pc[tid] = 0;     // histogram of hit counts
+                    int nh = 0;
+                    scan(nh);
+                    __syncwarp();
+                    if (__syncthreads_or(more)) {
+                        // some lane needs another pass: evaluate this one, then go on as usual
+                        once = false;
+                        evaluate(my_q, lane, nh, hp, hv, ax, ay, az, aw, ae);
+                        __syncwarp();
+                        break;
+                    }
+                    if (once) {
+                        // the pair of home beads b, b' is evaluated by the lower index
+                        // when b + b' is even, else by the higher, so that each bead
+                        // keeps about half of its home pairs; shares start at zero
+                        for (int e = tid; e < S; e += T) s_hidx[e] = -1;
+                        s_acc[3 * tid] = s_acc[3 * tid + 1] = s_acc[3 * tid + 2] = 0ull;
+                        __syncthreads();
+                        if (active) s_hidx[self_abs] = (int16_t)hb;
+                        __syncthreads();
+                        if (active) {   // drop the pairs the partner evaluates, keep the order
+                            int k = 0;
+                            for (int m = 0; m < nh; ++m) {
+                                const int e = my_q[m * 32 + lane];
+                                const int hj = s_hidx[e];
+                                if (hj < 0 || (((hb + hj) & 1) ? hb > hj : hb < hj))
+                                    my_q[(k++) * 32 + lane] = (uint16_t)e;
+                            }
+                            nh = k;
+                        }
+                    }
                     if (active) atomicAdd(&s_pc[PAIR_HMAX - nh], 1);
                     __syncthreads();
                     if (tid < 32) {   // bin starts, most hits first
@@ -1433,6 +1511,23 @@ __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int br
                     evaluate(s_q + (own >> 5) * PAIR_HMAX * 32, own & 31, on, ip, iv, bx, by, bz,
                              bw, be);
                     __syncwarp();
+                    if (once) {
+                        if (__syncthreads_or(wide)) {
+                            // a share too large for the fixed point: the brick again,
+                            // every pair from both ends (the scan restarts)
+                            once = false;
+                            r9 = 0;
+                            q = 0;
+                            more = active;
+                            continue;
+                        }
+                        if (tid < nact) {   // the bead's own sum, then its partners' shares
+                            const unsigned long long *acc = s_acc + 3 * own;
+                            bx = add_rn(bx, mul_rn((real)(long long)acc[0], (real)0x1p-41));
+                            by = add_rn(by, mul_rn((real)(long long)acc[1], (real)0x1p-41));
+                            bz = add_rn(bz, mul_rn((real)(long long)acc[2], (real)0x1p-41));
+                        }
+                    }
                     if (tid < nact) {
                         a.fpair[go] = mk4<vec4, real>(bx, by, bz, (real)0);
                         if (SAMPLE) a.ev[go] = mk4<vec4, real>(bw, be, (real)0, (real)0);
@@ -1441,9 +1536,7 @@ __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int br
                     __syncthreads();   // every queue read before the next scan
                     break;
                 }
-                // some lane needs another pass: evaluate this one, then go on as usual
-                evaluate(my_q, lane, nh, hp, hv, ax, ay, az, aw, ae);
-                __syncwarp();
+                if (done) break;
             }
             while (__any_sync(FULL, more)) {
                 int nh = 0;
@@ -1470,7 +1563,7 @@ __device__ __forceinline__ bool pair_brick(const PairLaunch<P> &la, const int br
 }
 
 template <class P, int T, bool SAMPLE>
-__global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : 1) k_pair(PairLaunch<P> la) {
+__global__ void __launch_bounds__(T, P::kOffsets ? PAIR_THREADS_PER_SM / T : (T <= PAIR64_THREADS_PER_SM ? PAIR64_THREADS_PER_SM / T : 1)) k_pair(PairLaunch<P> la) {
     griddep_wait();
     pair_brick<P, T, SAMPLE>(la, la.br_lo + blockIdx.x);
 }

@@ -16,7 +16,7 @@
 // ST_TIMEOUT).  The barrier words and the status are file-scope device
 // variables, cleared before the launch.
 //
-// dpd_bm_check: the FP64 Box-Muller logarithm and cosine (ln_u24, cos_u24)
+// dpd_bm_check: the FP64 Box-Muller logarithm and cosine (m2ln_u24 halved, cos_u24)
 // against the library's log and cospi over all 2^23 uniforms n 2^-24; returns
 // the largest absolute differences.
 #include <cuda_runtime.h>
@@ -55,7 +55,7 @@ __global__ void k_wait_check(int deliver, int tries) {
     if (threadIdx.x == 0 && buf[0] != g_wc_src[0]) atomicOr(&g_wc_status, dpd::ST_BADINPUT);
 }
 
-// |ln_u24(n) - log(n 2^-24)| and |cos_u24(n) - cospi(2 n 2^-24)| over every odd
+// |-m2ln_u24(n) / 2 - log(n 2^-24)| and |cos_u24(n) - cospi(2 n 2^-24)| over every odd
 // n < 2^24, their maxima kept as the bits of non-negative doubles (which order
 // like the doubles)
 __global__ void k_bm_check(const dpd::LnTab *t, unsigned long long *max_abs) {
@@ -64,7 +64,7 @@ __global__ void k_bm_check(const dpd::LnTab *t, unsigned long long *max_abs) {
          k += gridDim.x * blockDim.x) {
         const uint32_t n = 2u * k + 1u;
         const double u = (double)n * 0x1p-24;
-        ml = fmax(ml, fabs(dpd::ln_u24(n, t) - log(u)));
+        ml = fmax(ml, fabs(-0.5 * dpd::m2ln_u24(n, t) - log(u)));
         mc = fmax(mc, fabs(dpd::cos_u24(n) - cospi(2.0 * u)));
     }
     atomicMax(max_abs, (unsigned long long)__double_as_longlong(ml));

@@ -190,6 +190,26 @@ def test_inexact_brick_origins_match_oracle(D, prec, L, tile, threads):
     assert np.abs(d).max() < (1e-4 if prec == FP32 else 1e-9)
 
 
+def test_fp64_large_pair_forces_take_the_full_shell(D):
+    """FP64 evaluates each pair of two home beads once and hands the partner
+    its share in fixed point, which holds force components below 2^9; with
+    a_ij in the thousands most pairs exceed that, and the blocks redo their
+    bricks over the full shell.  Forces must still match the oracle, and runs
+    must repeat bit for bit."""
+    w = W.fluid(10.0, ntypes=2, a_same=2000.0, a_cross=2400.0, seed=31)
+    s = osys(w)
+    fo, _ = O.forces(s, O.wrap(s, w.pos), w.vel, 5)
+    outs = []
+    for _ in range(2):
+        g = gsys(D, w, FP64)
+        g.set_state(w.pos, w.vel, 5)
+        outs.append(g.get_state()[2])
+        g.close()
+    assert np.abs(fo).max() > 1e3
+    assert np.array_equal(outs[0], outs[1])
+    assert np.abs(outs[0] - fo).max() <= TOL[FP64] * np.abs(fo).max()
+
+
 @pytest.mark.parametrize("prec", [FP32, FP64])
 def test_uniform_noise_option(D, prec):
     w = WL["fluid_3k"]
