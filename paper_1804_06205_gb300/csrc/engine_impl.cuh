@@ -531,13 +531,15 @@ class BatchEngine : public BatchBase {
             err_ = "checkpoint buffer too small (see dpd_checkpoint_bytes)";
             return DPD_EINVAL;
         }
-        int rc = ensure_io((size_t)h.n);   // 72 B per bead: holds either record
-        if (rc) return rc;
         k_inv_perm<<<blocks(h.n), 256, 0, stream_>>>(h.bead0, h.n, id_[cur_], inv_perm_);
         ++launches_;
         DPD_CU(cudaGetLastError());
         CkptHeader hd;
         fill_header(h, hd);
+        // (records stored by the kernel straight into a page-locked host buffer
+        // took 0.76 ms at N = 3M, against 0.71 ms for the chunked copies below)
+        int rc = ensure_io((size_t)h.n);   // 72 B per bead: holds either record
+        if (rc) return rc;
         std::memcpy(buf, &hd, sizeof(hd));
         // records in chunks of ids, each copied to the host on the copy stream
         // while the next one is gathered
@@ -546,7 +548,7 @@ class BatchEngine : public BatchBase {
         const int nch = io_chunks(h.n);
         for (int c = 0; c < nch; ++c) {
             const int i0 = (int)((int64_t)h.n * c / nch), i1 = (int)((int64_t)h.n * (c + 1) / nch);
-            k_ckpt_out<P><<<blocks(i1 - i0), 256, 0, stream_>>>(s, i0, i1, sys_, pos_, key_,
+            k_ckpt_out<P><<<blocks(i1 - i0), CKPT_BLOCK, 0, stream_>>>(s, i0, i1, sys_, pos_, key_,
                                                                  vel_[cur_], frc_[cur_],
                                                                  inv_perm_, rio);
             ++launches_;
@@ -581,7 +583,8 @@ class BatchEngine : public BatchBase {
             return DPD_EINVAL;
         }
         const Rec *rec = reinterpret_cast<const Rec *>(static_cast<const char *>(buf) + sizeof(got));
-        if ((rc = ensure_io((size_t)h.n))) return rc;
+        const char *mh = static_cast<const char *>(mapped_host(buf));
+        if (!mh && (rc = ensure_io((size_t)h.n))) return rc;
         // the records go straight into the state arrays, in bead-id order: the
         // next step's position update takes the beads in any order and its cell
         // division puts them in the canonical order, so no sort is spent here;
@@ -599,12 +602,23 @@ class BatchEngine : public BatchBase {
         ia.count = nullptr;
         ia.id = id_[cur_];
         ia.status = status_;
-        // records copied in chunks on the copy stream, each restored as soon as
-        // it has landed (the staging buffer is free once earlier work is done)
+        // page-locked host buffer: the kernel reads the records there itself;
+        // else they are copied in chunks on the copy stream, each restored as
+        // soon as it has landed (the staging buffer is free once earlier work
+        // is done)
         Rec *rio = reinterpret_cast<Rec *>(io_);
-        DPD_CU(cudaEventRecord(xev_[IO_MAXCH], stream_));
-        DPD_CU(cudaStreamWaitEvent(xfer_, xev_[IO_MAXCH], 0));
-        const int nch = io_chunks(h.n);
+        const int nch = mh ? 0 : io_chunks(h.n);
+        if (mh) {
+            ia.i0 = 0;
+            ia.i1 = h.n;
+            k_ckpt_in<P><<<blocks(h.n), CKPT_BLOCK, 0, stream_>>>(
+                ia, reinterpret_cast<const Rec *>(mh + sizeof(got)));
+            ++launches_;
+            DPD_CU(cudaGetLastError());
+        } else {
+            DPD_CU(cudaEventRecord(xev_[IO_MAXCH], stream_));
+            DPD_CU(cudaStreamWaitEvent(xfer_, xev_[IO_MAXCH], 0));
+        }
         for (int c = 0; c < nch; ++c) {
             const int i0 = (int)((int64_t)h.n * c / nch), i1 = (int)((int64_t)h.n * (c + 1) / nch);
             DPD_CU(cudaMemcpyAsync(rio + i0, rec + i0, (size_t)(i1 - i0) * sizeof(Rec),
@@ -613,7 +627,7 @@ class BatchEngine : public BatchBase {
             DPD_CU(cudaStreamWaitEvent(stream_, xev_[c], 0));
             ia.i0 = i0;
             ia.i1 = i1;
-            k_ckpt_in<P><<<blocks(i1 - i0), 256, 0, stream_>>>(ia, rio);
+            k_ckpt_in<P><<<blocks(i1 - i0), CKPT_BLOCK, 0, stream_>>>(ia, rio);
             ++launches_;
             DPD_CU(cudaGetLastError());
         }
@@ -760,6 +774,21 @@ class BatchEngine : public BatchBase {
 
     // chunks of a host <-> device state transfer: at least IO_CHUNK beads each
     static int io_chunks(int n) { return std::max(1, std::min(IO_MAXCH, n / IO_CHUNK)); }
+    // The device address of a caller's buffer that is page-locked host memory
+    // mapped into the device's address space (cudaHostAlloc, cudaHostRegister)
+    // and 8-byte aligned, so that kernels read or write it over the host link
+    // with no copy of their own; null for any other buffer.
+    static void *mapped_host(const void *buf) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, buf) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        if (at.type != cudaMemoryTypeHost || !at.devicePointer ||
+            (reinterpret_cast<uintptr_t>(at.devicePointer) & 7u) != 0)
+            return nullptr;
+        return at.devicePointer;
+    }
 
     int peek_status() { return status_host_; }
 

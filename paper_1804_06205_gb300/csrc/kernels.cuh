@@ -1912,41 +1912,72 @@ struct CkptRec<PF64> {
     using type = CkptRec64;
 };
 
+// The records of a block (256 ids) move between the record array and shared
+// memory as 8-byte words, so a warp's accesses are contiguous: the array may be
+// host memory that the kernel reads or writes directly over the host link.
+// The array must be 8-byte aligned (records are multiples of 8 bytes).
+constexpr int CKPT_BLOCK = 256;
+
 template <class P>
-__global__ void __launch_bounds__(256) k_ckpt_out(int s, int i0, int i1, const SysDesc<P> *sys,
-                                                  const typename P::vec4 *pos, const uint32_t *key,
-                                                  const typename P::vec4 *vel,
-                                                  const typename P::vec4 *frc,
-                                                  const int32_t *inv_perm,
-                                                  typename CkptRec<P>::type *out) {
+__global__ void __launch_bounds__(CKPT_BLOCK) k_ckpt_out(int s, int i0, int i1, const SysDesc<P> *sys,
+                                                         const typename P::vec4 *pos, const uint32_t *key,
+                                                         const typename P::vec4 *vel,
+                                                         const typename P::vec4 *frc,
+                                                         const int32_t *inv_perm,
+                                                         typename CkptRec<P>::type *out) {
+    using Rec = typename CkptRec<P>::type;
+    constexpr int W = (int)(sizeof(Rec) / 8);
+    static_assert(sizeof(Rec) % 8 == 0, "records are whole 8-byte words");
+    __shared__ __align__(16) uint2 s_w[CKPT_BLOCK * W];
     const SysDesc<P> &D = sys[s];
-    const int i = i0 + blockIdx.x * blockDim.x + threadIdx.x;   // ids [i0, i1)
-    if (i >= i1) return;
-    const int t = inv_perm[D.bead0 + i];
-    const typename P::vec4 p = pos[t], v = vel[t], f = frc[t];
-    typename CkptRec<P>::type r;
-    if constexpr (P::kOffsets) {
-        r.key = key[t];
-        r.o[0] = p.x; r.o[1] = p.y; r.o[2] = p.z;
-    } else {
-        r.x[0] = p.x; r.x[1] = p.y; r.x[2] = p.z;
+    const int b0 = i0 + blockIdx.x * CKPT_BLOCK;   // ids [b0, b0 + cnt) of [i0, i1)
+    const int cnt = min(CKPT_BLOCK, i1 - b0);
+    const int i = b0 + threadIdx.x;
+    if (i < i1) {
+        const int t = inv_perm[D.bead0 + i];
+        const typename P::vec4 p = pos[t], v = vel[t], f = frc[t];
+        Rec r;
+        if constexpr (P::kOffsets) {
+            r.key = key[t];
+            r.o[0] = p.x; r.o[1] = p.y; r.o[2] = p.z;
+        } else {
+            r.x[0] = p.x; r.x[1] = p.y; r.x[2] = p.z;
+        }
+        r.v[0] = v.x; r.v[1] = v.y; r.v[2] = v.z;
+        r.f[0] = f.x; r.f[1] = f.y; r.f[2] = f.z;
+        reinterpret_cast<Rec *>(s_w)[threadIdx.x] = r;
     }
-    r.v[0] = v.x; r.v[1] = v.y; r.v[2] = v.z;
-    r.f[0] = f.x; r.f[1] = f.y; r.f[2] = f.z;
-    out[i] = r;
+    __syncthreads();
+    uint2 *dst = reinterpret_cast<uint2 *>(out + b0);
+    if ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {   // 16-byte words, an 8-byte tail
+        const int n16 = cnt * W / 2;
+        for (int k = threadIdx.x; k < n16; k += CKPT_BLOCK)
+            reinterpret_cast<uint4 *>(dst)[k] = reinterpret_cast<const uint4 *>(s_w)[k];
+        if (((cnt * W) & 1) && threadIdx.x == 0) dst[2 * n16] = s_w[2 * n16];
+    } else {
+        for (int k = threadIdx.x; k < cnt * W; k += CKPT_BLOCK) dst[k] = s_w[k];
+    }
 }
 
 // Restore: like the initial binning (k_init), from checkpoint records; a
 // non-finite value or an FP32 key beyond the system's cells sets ST_BADINPUT.
 template <class P>
-__global__ void __launch_bounds__(256) k_ckpt_in(InitArgs<P> a,
-                                                 const typename CkptRec<P>::type *rec) {
+__global__ void __launch_bounds__(CKPT_BLOCK) k_ckpt_in(InitArgs<P> a,
+                                                        const typename CkptRec<P>::type *rec) {
     using real = typename P::real;
+    using Rec = typename CkptRec<P>::type;
+    constexpr int W = (int)(sizeof(Rec) / 8);
+    __shared__ uint2 s_w[CKPT_BLOCK * W];
     const SysDesc<P> &D = a.sys[a.s];
-    const int i = a.i0 + blockIdx.x * blockDim.x + threadIdx.x;
+    const int b0 = a.i0 + blockIdx.x * CKPT_BLOCK;   // ids [b0, b0 + cnt) of [i0, i1)
+    const int cnt = min(CKPT_BLOCK, a.i1 - b0);
+    const uint2 *src = reinterpret_cast<const uint2 *>(rec + b0);
+    for (int k = threadIdx.x; k < cnt * W; k += CKPT_BLOCK) s_w[k] = src[k];
+    __syncthreads();
+    const int i = b0 + threadIdx.x;
     if (i >= a.i1) return;
     const int t = D.bead0 + i;
-    const typename CkptRec<P>::type r = rec[i];
+    const Rec r = reinterpret_cast<const Rec *>(s_w)[threadIdx.x];
     typename P::vec4 out;
     uint32_t key;
     bool fin = isfinite(r.v[0]) && isfinite(r.v[1]) && isfinite(r.v[2]) && isfinite(r.f[0]) &&

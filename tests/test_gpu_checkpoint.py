@@ -178,3 +178,42 @@ def test_checkpoint_rejects_foreign_or_damaged_data(D):
     assert g.get_state()[3] == 3
     for x in (g, g64, gs):
         x.close()
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_pinned_host_buffers_are_restored_in_place(D, prec):
+    """A page-locked host buffer is read by the restore kernel directly over
+    the host link; an unaligned one (offset by 4 bytes) and pageable memory go
+    through the chunked copies, as every read-out does.  All give the same
+    bytes, and a run resumed from each equals the uninterrupted run bit for
+    bit."""
+    import torch
+    w = W.fluid(24.5, ntypes=2, a_same=25.0, a_cross=30.0, seed=67)
+    n = 2
+    ref = _straight(D, w, prec, n)
+    g = D.System.from_workload(w, precision=prec)
+    g.set_state(w.pos, w.vel, 0)
+    g.step(n)
+    ck = g.get_checkpoint()          # pageable bytes: the copy path
+    nb = g.checkpoint_bytes()
+    assert nb == len(ck)
+    pin = torch.zeros(nb + 16, dtype=torch.uint8, pin_memory=True)
+    base = pin.data_ptr()
+    assert base % 8 == 0
+    for off in (0, 4):               # read-outs into pinned memory, aligned or not
+        pin.zero_()
+        g.get_checkpoint_ptr(base + off, nb)
+        assert pin.numpy()[off:off + nb].tobytes() == ck
+    g.close()
+    for off in (0, 4):
+        pin.zero_()
+        pin.numpy()[off:off + nb] = np.frombuffer(ck, dtype=np.uint8)
+        h = D.System.from_workload(w, precision=prec)
+        h.set_checkpoint_ptr(base + off, nb)
+        assert h.get_checkpoint() == ck
+        h.step(n)
+        out = h.get_state()
+        h.close()
+        for a, b in zip(ref[:3], out[:3]):
+            assert np.array_equal(a, b)
+        assert out[3] == ref[3]
